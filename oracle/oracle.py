@@ -1,0 +1,231 @@
+"""ctypes front-end of the plain C FP64 oracle (smg_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the package smoke check and
+by the benchmark's CPU-baseline leg, never by the product path.  The shared
+library is compiled from source with gcc on first use (or by ``build()``).
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "smg_oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+ORC_OK, ORC_EINVAL, ORC_ENOMEM, ORC_EBREAKDOWN, ORC_ENOTCONV, ORC_ENAN = 0, 1, 2, 4, 5, 6
+SGS, ILU0 = 0, 1
+FW27V, PC8C = 0, 1
+FP64, FP32, BF16 = 0, 1, 2
+
+
+def build(force=False):
+    """Compile liboracle.so (plain C, -O2, no FMA contraction)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_SO)
+        _lib.orc_bf16_round.restype = ctypes.c_float
+        _lib.orc_bf16_round.argtypes = [ctypes.c_double]
+        _lib.orc_mg_level_array.restype = ctypes.c_long
+        _lib.orc_mg_free.argtypes = [ctypes.c_void_p]
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _i3(d):
+    return np.ascontiguousarray(np.asarray(d, dtype=np.int32).reshape(3))
+
+
+def _offs(off):
+    return np.ascontiguousarray(np.asarray(off, dtype=np.int32).reshape(-1, 3))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def npts(d):
+    return int(d[0]) * int(d[1]) * int(d[2])
+
+
+def mask_validate(off):
+    o = _offs(off)
+    return lib().orc_mask_validate(len(o), _p(o))
+
+
+def spmv(d, off, A, x, B=1):
+    d, o, A, x = _i3(d), _offs(off), _f64(A), _f64(x)
+    y = np.zeros(npts(d) * B)
+    lib().orc_spmv(_p(d), len(o), _p(o), B, _p(A), _p(x), _p(y))
+    return y
+
+
+def residual(d, off, A, b, x, B=1):
+    d, o, A, b, x = _i3(d), _offs(off), _f64(A), _f64(b), _f64(x)
+    r = np.zeros(npts(d) * B)
+    lib().orc_residual(_p(d), len(o), _p(o), B, _p(A), _p(b), _p(x), _p(r))
+    return r
+
+
+def diag_inverse(d, off, A, B=1):
+    d, o, A = _i3(d), _offs(off), _f64(A)
+    D = np.zeros(npts(d) * B * B)
+    rc = lib().orc_diag_inverse(_p(d), len(o), _p(o), B, _p(A), _p(D))
+    if rc:
+        raise ArithmeticError("zero diagonal")
+    return D
+
+
+def gs_forward(d, off, A, Dinv, b, u, w=1.0, B=1):
+    d, o, A, Dinv, b = _i3(d), _offs(off), _f64(A), _f64(Dinv), _f64(b)
+    u = _f64(u).copy()
+    lib().orc_gs_forward(_p(d), len(o), _p(o), B, _p(A), _p(Dinv), _p(b), _p(u), ctypes.c_double(w))
+    return u
+
+
+def gs_backward(d, off, A, Dinv, b, u, w=1.0, B=1):
+    d, o, A, Dinv, b = _i3(d), _offs(off), _f64(A), _f64(Dinv), _f64(b)
+    u = _f64(u).copy()
+    lib().orc_gs_backward(_p(d), len(o), _p(o), B, _p(A), _p(Dinv), _p(b), _p(u), ctypes.c_double(w))
+    return u
+
+
+def ilu0_factor(d, off, A, spd_check=True):
+    d, o, A = _i3(d), _offs(off), _f64(A)
+    LU = np.zeros_like(A)
+    rc = lib().orc_ilu0_factor(_p(d), len(o), _p(o), _p(A), _p(LU), int(spd_check))
+    if rc:
+        raise ArithmeticError("ILU(0) breakdown")
+    return LU
+
+
+def ilu0_apply(d, off, LU, Udinv, r):
+    d, o, LU, Udinv, r = _i3(d), _offs(off), _f64(LU), _f64(Udinv), _f64(r)
+    x = np.zeros_like(r)
+    lib().orc_ilu0_apply(_p(d), len(o), _p(o), _p(LU), _p(Udinv), _p(r), _p(x))
+    return x
+
+
+def coarse_dims(d):
+    return [int(t) // 2 for t in d]
+
+
+def restrict(transfer, fd, rf, B=1):
+    fd, rf = _i3(fd), _f64(rf)
+    fc = np.zeros(npts(coarse_dims(fd)) * B)
+    lib().orc_restrict(transfer, _p(fd), B, _p(rf), _p(fc))
+    return fc
+
+
+def prolong_add(transfer, fd, ec, uf, B=1):
+    fd, ec = _i3(fd), _f64(ec)
+    uf = _f64(uf).copy()
+    lib().orc_prolong_add(transfer, _p(fd), B, _p(ec), _p(uf))
+    return uf
+
+
+def rap27(transfer, fd, off, Af, B=1):
+    """Brute-force Galerkin product.  Returns (Ac27 [nc,27,B,B], present[27])."""
+    fd, o, Af = _i3(fd), _offs(off), _f64(Af)
+    nc = npts(coarse_dims(fd))
+    Ac = np.zeros(nc * 27 * B * B)
+    present = np.zeros(27, dtype=np.int32)
+    rc = lib().orc_rap27(transfer, _p(fd), len(o), _p(o), B, _p(Af), _p(Ac), _p(present))
+    if rc:
+        raise ValueError("coarse offset outside {-1,0,1}^3")
+    return Ac.reshape(nc, 27, B, B), present
+
+
+def assemble_dense(d, off, A, B=1):
+    d, o, A = _i3(d), _offs(off), _f64(A)
+    n = npts(d) * B
+    M = np.zeros((n, n))
+    lib().orc_assemble_dense(_p(d), len(o), _p(o), B, _p(A), _p(M))
+    return M
+
+
+def bf16_round(x):
+    return lib().orc_bf16_round(float(x))
+
+
+def plan_levels(d, max_levels=16):
+    d = _i3(d)
+    out = np.zeros((16, 3), dtype=np.int32)
+    L = lib().orc_plan_levels(_p(d), max_levels, _p(out))
+    return [tuple(int(t) for t in out[l]) for l in range(L)]
+
+
+class MG:
+    """Oracle multigrid hierarchy (V(1,1)-cycle preconditioner + Krylov)."""
+
+    def __init__(self, d, off, A, B=1, smoother=SGS, transfer=FW27V, w=1.0, precision=FP64, max_levels=16):
+        d, o, A = _i3(d), _offs(off), _f64(A)
+        h = ctypes.c_void_p()
+        rc = lib().orc_mg_setup(ctypes.byref(h), _p(d), len(o), _p(o), B, _p(A), smoother, transfer,
+                                ctypes.c_double(w), precision, max_levels)
+        if rc:
+            raise ValueError("oracle setup failed: %d" % rc)
+        self.h, self.B, self.dims = h, B, tuple(int(t) for t in d)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.orc_mg_free(self.h)
+            self.h = None
+
+    @property
+    def nlevels(self):
+        return lib().orc_mg_nlevels(self.h)
+
+    def level_info(self, l):
+        d = np.zeros(3, dtype=np.int32)
+        ns = ctypes.c_int()
+        off = np.zeros((27, 3), dtype=np.int32)
+        lib().orc_mg_level_info(self.h, l, _p(d), ctypes.byref(ns), _p(off))
+        return tuple(int(t) for t in d), off[: ns.value].copy()
+
+    def level_array(self, l, which):
+        n = lib().orc_mg_level_array(self.h, l, which, None)
+        dt = np.float64 if which <= 2 else np.float32
+        out = np.zeros(n, dtype=dt)
+        if n:
+            lib().orc_mg_level_array(self.h, l, which, _p(out))
+        return out
+
+    def vcycle(self, r):
+        r = _f64(r)
+        z = np.zeros_like(r)
+        lib().orc_mg_vcycle(self.h, _p(r), _p(z))
+        return z
+
+    def pcg(self, b, x0=None, tol=1e-9, maxit=200, flexible=False):
+        b = _f64(b)
+        x = np.zeros_like(b) if x0 is None else _f64(x0).copy()
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        hist = np.zeros(maxit + 1)
+        rc = lib().orc_pcg(self.h, _p(b), _p(x), ctypes.c_double(tol), maxit, int(flexible),
+                           ctypes.byref(it), ctypes.byref(rr), _p(hist))
+        return x, rc, it.value, rr.value, hist[: it.value + 1]
+
+    def fgmres(self, b, x0=None, tol=1e-8, maxit=200, restart=30):
+        b = _f64(b)
+        x = np.zeros_like(b) if x0 is None else _f64(x0).copy()
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        hist = np.zeros(maxit + 1)
+        rc = lib().orc_fgmres(self.h, _p(b), _p(x), ctypes.c_double(tol), maxit, restart,
+                              ctypes.byref(it), ctypes.byref(rr), _p(hist))
+        return x, rc, it.value, rr.value, hist[: it.value + 1]
