@@ -1,0 +1,220 @@
+/*
+ * smg.h -- C ABI of the GB300 structured-multigrid library (StructMG method,
+ * arXiv 2506.21932): stencil Galerkin coarsening, dependence-preserving
+ * Gauss-Seidel / ILU(0) smoothers, V-cycle preconditioned PCG / FGMRES.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid and vectors (Sec. 4.1, SG-DIA format): a structured grid of
+ *   nx * ny * nz points; point (i,j,k) has linear index p = (i*ny + j)*nz + k
+ *   (x slowest, z fastest).  A vector holds B values per point: v[p*B + r].
+ * Matrices (Sec. 4.1, SG-DIA): for every point, one coefficient (B == 1) or
+ *   one row-major BxB block (B == 3) per stencil offset, offsets in
+ *   {-1,0,1}^3 (Sec. 4.2, "Extensibility & Flexibility"):
+ *   A[((p*nstencil + e)*B + r)*B + c].  Coefficients whose neighbour lies off
+ *   the grid must be 0 (zero padding).  The offset list may be given in any
+ *   order but must contain the centre, no duplicates and be structurally
+ *   symmetric; the library stores it in lexicographic order (dx slowest).
+ * Memory: every pointer argument documented "device" is CUDA device memory
+ *   owned by the caller; the library never frees or keeps it after the call
+ *   returns (coefficients are copied at setup).  "host" pointers are ordinary
+ *   host memory.  All work is enqueued on the caller's CUDA stream (a
+ *   cudaStream_t passed as void*; NULL = legacy default stream) and the calls
+ *   return after that work has completed unless stated otherwise.
+ * Errors: every function returns an smg_status; nothing is thrown and no
+ *   device trap is ever raised.  Device-side waits are bounded; a wait that
+ *   runs out returns SMG_ETIMEOUT and leaves the context reusable.
+ * Threads: one context must not be used from two threads at once.
+ */
+#ifndef SMG_H
+#define SMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smg_ctx* smg_t;
+
+typedef enum {
+  SMG_OK = 0,
+  SMG_EINVAL = 1,      /* bad argument: sizes, mask, options, off-grid coefficient != 0 */
+  SMG_ENOMEM = 2,      /* device allocation failed */
+  SMG_ECUDA = 3,       /* a CUDA runtime call failed */
+  SMG_EBREAKDOWN = 4,  /* zero/negative pivot, zero diagonal, p^T A p <= 0 */
+  SMG_ENOTCONV = 5,    /* tolerance not reached within maxit iterations */
+  SMG_ENAN = 6,        /* non-finite residual */
+  SMG_ETIMEOUT = 7     /* a bounded device-side wait ran out */
+} smg_status;
+
+enum { SMG_SMOOTHER_SGS = 0, SMG_SMOOTHER_ILU0 = 1 };
+enum { SMG_TRANSFER_FW27V = 0, SMG_TRANSFER_PC8C = 1 };
+enum { SMG_PREC_FP64 = 0, SMG_PREC_FP32 = 1, SMG_PREC_BF16 = 2 };
+enum { SMG_KRYLOV_PCG = 0, SMG_KRYLOV_FPCG = 1, SMG_KRYLOV_FGMRES = 2 };
+
+/* Solver options; an all-zero struct selects the defaults in brackets.
+ *  smoother   [SGS]  symmetric lexicographic Gauss-Seidel (Sec. 4.4 GS-Forward
+ *                    then GS-Backward) or ILU(0) on the matrix mask (Sec. 4.4
+ *                    ILU formula; Sec. 4.2 ILU masks).  One pre- and one
+ *                    post-smoothing step per level (Sec. 5.2); the first
+ *                    pre-smoothing starts from zero (ZeroGuess, Table 8).
+ *  transfer   [FW27V] vertex full weighting: coarse I on fine 2I+1, trilinear
+ *                    P and R = P^T/8 (Table 3 pattern 3d27v); PC8C: cell
+ *                    piecewise constant, R(I,u)=1 on u in 2I+{0,1}^3, P = R^T
+ *                    (Table 3 pattern 3d8c).
+ *  precision  [FP64] storage and arithmetic of the hierarchy and V-cycle:
+ *                    FP64, FP32, or BF16 values with one FP32 scale per row
+ *                    and FP32 accumulation (not in the paper).  The Krylov
+ *                    iteration, the outer residual and the coarsest solve stay
+ *                    FP64.  BF16 requires block == 1.
+ *  krylov     [PCG]  PCG, flexible PCG (Polak-Ribiere beta) or right-
+ *                    preconditioned flexible GMRES(restart) (Sec. 5.2).
+ *  restart    [30]   GMRES restart length, 1..64.
+ *  relax_w    [1.0]  Gauss-Seidel weight w of the Sec. 4.4 formulas.
+ *  max_levels [16]   cap on the number of levels (>= 1).
+ *  spin_budget_ms [1000] bound on any single device-side wait, in ms.
+ *  use_graph  [0]    1: capture each V-cycle in a CUDA graph and replay it. */
+typedef struct {
+  int smoother, transfer, precision, krylov, restart;
+  double relax_w;
+  int max_levels;
+  int spin_budget_ms;
+  int use_graph;
+} smg_options;
+
+/* Build the hierarchy from the finest matrix (Sec. 4.2 "Input Data Format":
+ * only the finest A is given).  Levels: halve every dimension while all are
+ * even and the smallest is >= 8 (stride-2 full coarsening, Sec. 4.1 P2).
+ * Coarse operators: Galerkin A^C = R A^F P (Eq. 4) evaluated per coarse point
+ * by influence chains (Eq. 5-10) derived once on the host from the (R, A, P)
+ * patterns.  Smoother set-up per level; dense LU-based inverse of the coarsest
+ * level (the paper does not specify the coarsest solve).
+ *  out      host: receives the new context (NULL on failure).
+ *  dims     host int[3] = {nx, ny, nz}, each >= 1 and <= 4096, ny <= 1024.
+ *  nstencil number of offsets, 1..27;  offsets host int[nstencil][3].
+ *  coeffs   device double, layout above; read during the call only.
+ *  block    B = 1 or 3 (3 = three coupled unknowns per point, block GS).
+ *  opt      host, may be NULL (all defaults).
+ *  stream   cudaStream_t.
+ * Errors: SMG_EINVAL (bad sizes/mask/options, nonzero off-grid coefficient),
+ * SMG_ENOMEM, SMG_EBREAKDOWN (zero diagonal, ILU pivot <= 0, singular
+ * coarsest matrix), SMG_ECUDA, SMG_ETIMEOUT. */
+int smg_setup(smg_t* out, const int dims[3], int nstencil, const int* offsets, const double* coeffs, int block,
+              const smg_options* opt, void* stream);
+
+/* One V(1,1)-cycle as preconditioner: z = M^{-1} r (Sec. 2, Fig. 1 V-cycle).
+ *  r, z  device double [n*B]; may not alias.
+ * Errors: SMG_EINVAL (NULL handle/pointers), SMG_ECUDA, SMG_ETIMEOUT. */
+int smg_vcycle(smg_t h, const double* r, double* z, void* stream);
+
+/* Solve A x = b with the Krylov method of the options, preconditioned by one
+ * V-cycle per iteration (Sec. 5.2), until ||r_k||_2 / ||b||_2 < tol (Table 8).
+ *  b      device double [n*B];  x  device double [n*B]: initial guess in,
+ *         solution out.
+ *  tol    relative tolerance > 0;  maxit  >= 0 iterations.
+ *  iters  host int*, may be NULL: iterations taken.
+ *  relres host double*, may be NULL: TRUE relative residual ||b-Ax||/||b||
+ *         recomputed in FP64 at exit.
+ * Errors: SMG_ENOTCONV (iters = maxit), SMG_EBREAKDOWN (p^T A p <= 0 in CG),
+ * SMG_ENAN, SMG_EINVAL, SMG_ECUDA, SMG_ETIMEOUT. */
+int smg_solve(smg_t h, const double* b, double* x, double tol, int maxit, int* iters, double* relres, void* stream);
+
+/* Hierarchy statistics (Eq. 2 complexities, Sec. 6.2).
+ *  grid_complexity = sum_l n_l / n_0;  operator_complexity = sum_l n_l*ns_l /
+ *  (n_0*ns_0) (SG-DIA storage counts every row as ns_l entries);
+ *  vcycle_bytes = algorithmic HBM bytes of one V-cycle (each array touched
+ *  once per kernel); setup_ms = device time of the last smg_setup. */
+typedef struct {
+  int levels;
+  int dims[16][3];
+  int nstencil[16];
+  double grid_complexity, operator_complexity;
+  double vcycle_bytes, vcycle_fp64_flops;
+  double setup_ms;
+  int precision, smoother, transfer, block;
+} smg_stats_t;
+int smg_stats(smg_t h, smg_stats_t* out);
+
+void smg_destroy(smg_t h);
+const char* smg_strerror(int status);
+
+/* ---------------------------------------------------------------------------
+ * Level-wise building blocks.  They run the same kernels as the V-cycle, one
+ * at a time, on the hierarchy's own level data, for callers that compose
+ * their own cycle and for parity testing.  Level 0 is the finest.
+ * ------------------------------------------------------------------------- */
+
+/* Number of levels, and dims / stencil (lexicographic offsets, int[27][3])
+ * of level l.  Errors: SMG_EINVAL for a bad handle or level. */
+int smg_level_count(smg_t h);
+int smg_level_info(smg_t h, int l, int dims[3], int* nstencil, int* offsets);
+
+/* Copy a level array into caller device memory `dst` of `bytes` bytes.
+ * which: 0 A (double, layout above), 1 ILU(0) factors (double [n][ns]: unit-
+ * lower L on lower offsets, U on centre and upper offsets), 2 inverse
+ * diagonal (double: [n] for B == 1 / 1/u_pp for ILU, [n][B][B] for B == 3),
+ * 3 low-precision matrix values ([n][ns] float for FP32, bf16 bits as
+ * uint16 for BF16), 4 FP32 row scale of A [n], 5 low-precision ILU factors
+ * ([n][ns] like 3: lower entries scaled by 6, upper by 7), 6 FP32 row scale of
+ * L [n], 7 FP32 row scale of U [n], 8 FP32 inverse diagonal [n].
+ * Returns SMG_EINVAL if the array does not exist on that level or bytes is
+ * smaller than its size; writes the size to *needed if not NULL. */
+int smg_level_copy(smg_t h, int l, int which, void* dst, size_t bytes, size_t* needed, void* stream);
+
+/* Level operations (vectors are device arrays in the level's V-cycle
+ * precision: double for FP64 hierarchies, float otherwise; B values/point).
+ *  SMG_OP_SPMV         y = A x                               (x, -, y)
+ *  SMG_OP_RESIDUAL     y = b - A x                           (x, b, y)
+ *  SMG_OP_GS_FORWARD   x <- GS-Forward sweep on A x = b      (x, b, -) in place
+ *  SMG_OP_GS_BACKWARD  x <- GS-Backward sweep                (x, b, -) in place
+ *  SMG_OP_GS_ZERO      x <- GS-Forward from x = 0 (ZeroGuess) (x, b, -)
+ *  SMG_OP_ILU_APPLY    y = U^{-1} L^{-1} b                    (-, b, y)
+ *  SMG_OP_RESTRICT     y(level l+1) = R x(level l)           (x, -, y)
+ *  SMG_OP_PROLONG_ADD  y(level l) += P x(level l+1)          (x, -, y)
+ *  SMG_OP_COARSE_SOLVE y = A_c^{-1} b on the coarsest level (-, b, y), double
+ *  SMG_OP_ILU_LOWER    y = L^{-1} b (unit lower solve only; y may equal b)
+ *  SMG_OP_ILU_UPPER    y = U^{-1} b (upper solve only; y may equal b)
+ * A one-level hierarchy keeps its smoother data, so the sweeps are available
+ * on level 0 even when it is also the coarsest level.
+ * Errors: SMG_EINVAL (bad level/op/missing smoother data), SMG_ECUDA,
+ * SMG_ETIMEOUT. */
+enum {
+  SMG_OP_SPMV = 0, SMG_OP_RESIDUAL = 1, SMG_OP_GS_FORWARD = 2, SMG_OP_GS_BACKWARD = 3, SMG_OP_GS_ZERO = 4,
+  SMG_OP_ILU_APPLY = 5, SMG_OP_RESTRICT = 6, SMG_OP_PROLONG_ADD = 7, SMG_OP_COARSE_SOLVE = 8,
+  SMG_OP_ILU_LOWER = 9, SMG_OP_ILU_UPPER = 10
+};
+int smg_level_apply(smg_t h, int l, int op, const void* x, const void* b, void* y, void* stream);
+
+/* Number of CUDA kernels this library has enqueued since it was loaded (a
+ * V-cycle replayed from a CUDA graph counts its kernels on every replay).
+ * Host-only; never fails. */
+long long smg_launch_count(void);
+
+/* Failure-path self-test of the bounded device waits: launches one wait on a
+ * device flag that nothing ever sets, with a budget of budget_ms (1..10000).
+ * Returns SMG_ETIMEOUT when the wait ran out as designed (the context stays
+ * usable), SMG_EINVAL for bad arguments, SMG_ECUDA on a CUDA failure. */
+int smg_selftest_wait(smg_t h, int budget_ms, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Host-only symbolic derivation of influence chains (Sec. 4.3, Eq. 5-10).
+ * Given R, A^F, P patterns as fine-grid offsets -- R and P relative to the
+ * fine anchor of their coarse point, A relative to the fine point -- a chain
+ * (r, a, q) links coarse point I to coarse neighbour I + dJ when
+ * roff[r] + aoff[a] - poff[q] = 2*dJ (stride-2 coarsening).  dim = 2 or 3
+ * (z components ignored/zero for 2).  Writes up to max_chains chains as
+ * int[5] {r, a, q, dJ lexicographic index in {-1,0,1}^dim, 0} and returns the
+ * total chain count, or -1 if a chain reaches a coarse offset outside
+ * {-1,0,1}^dim or an argument is invalid.  No GPU is used.
+ * ------------------------------------------------------------------------- */
+int smg_derive_chains(int dim, int nr, const int* roff, int na, const int* aoff, int np, const int* poff,
+                      int max_chains, int* chains);
+
+/* Library version string. */
+const char* smg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMG_H */

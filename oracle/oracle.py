@@ -151,6 +151,18 @@ def rap27(transfer, fd, off, Af, B=1):
     return Ac.reshape(nc, 27, B, B), present
 
 
+def rap27_at(transfer, fd, off, Af, points, B=1):
+    """Brute-force Galerkin coefficients of the listed coarse points only:
+    returns [len(points), 27, B, B] (all 27 offsets, lexicographic)."""
+    fd, o, Af = _i3(fd), _offs(off), _f64(Af)
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int64))
+    out = np.zeros(len(pts) * 27 * B * B)
+    rc = lib().orc_rap27_at(transfer, _p(fd), len(o), _p(o), B, _p(Af), ctypes.c_long(len(pts)), _p(pts), _p(out))
+    if rc:
+        raise ValueError("coarse offset outside {-1,0,1}^3")
+    return out.reshape(len(pts), 27, B, B)
+
+
 def assemble_dense(d, off, A, B=1):
     d, o, A = _i3(d), _offs(off), _f64(A)
     n = npts(d) * B

@@ -379,6 +379,41 @@ void orc_prolong_add(int transfer, const int fd[3], int B, const double* ec, dou
  * lexicographic order (dx slowest): Ac27[((P*27 + o)*B + r)*B + c].
  * present[o] is set when some chain reaches offset o.  Returns ORC_EINVAL if a
  * chain reaches a coarse offset outside {-1,0,1}^3. */
+/* All chains of one coarse point I, accumulated into out27[27][B][B]. */
+static int rap_point(int transfer, const int fd[3], const int cd[3], int ns, const int* off, int B, const double* Af,
+                     const int I[3], double* out27, int* present) {
+  int base[3], span;
+  support(transfer, I, base, &span);
+  for (int a = 0; a < span; ++a)
+    for (int b = 0; b < span; ++b)
+      for (int c = 0; c < span; ++c) {
+        int u[3] = {base[0] + a, base[1] + b, base[2] + c};
+        if (!inside(fd, u[0], u[1], u[2])) continue;
+        double wr = rweight(transfer, I, u);
+        if (wr == 0.0) continue;
+        long pu = pidx(fd, u[0], u[1], u[2]);
+        for (int e = 0; e < ns; ++e) {
+          int v[3] = {u[0] + off[3 * e], u[1] + off[3 * e + 1], u[2] + off[3 * e + 2]};
+          if (!inside(fd, v[0], v[1], v[2])) continue;
+          for (int ja = -2; ja <= 2; ++ja)
+            for (int jb = -2; jb <= 2; ++jb)
+              for (int jc = -2; jc <= 2; ++jc) {
+                int J[3] = {I[0] + ja, I[1] + jb, I[2] + jc};
+                if (!inside(cd, J[0], J[1], J[2])) continue;
+                double wp = pweight(transfer, v, J);
+                if (wp == 0.0) continue;
+                if (ja < -1 || ja > 1 || jb < -1 || jb > 1 || jc < -1 || jc > 1) return ORC_EINVAL;
+                int o = (ja + 1) * 9 + (jb + 1) * 3 + (jc + 1);
+                present[o] = 1;
+                for (int r = 0; r < B; ++r)
+                  for (int cc = 0; cc < B; ++cc)
+                    out27[(o * B + r) * B + cc] += wr * Af[((pu * ns + e) * B + r) * B + cc] * wp;
+              }
+        }
+      }
+  return ORC_OK;
+}
+
 int orc_rap27(int transfer, const int fd[3], int ns, const int* off, int B, const double* Af, double* Ac27,
               int* present) {
   int cd[3];
@@ -389,37 +424,27 @@ int orc_rap27(int transfer, const int fd[3], int ns, const int* off, int B, cons
   for (int I0 = 0; I0 < cd[0]; ++I0)
     for (int I1 = 0; I1 < cd[1]; ++I1)
       for (int I2 = 0; I2 < cd[2]; ++I2) {
-        int I[3] = {I0, I1, I2}, base[3], span;
-        support(transfer, I, base, &span);
+        int I[3] = {I0, I1, I2};
         long Pc = pidx(cd, I0, I1, I2);
-        for (int a = 0; a < span; ++a)
-          for (int b = 0; b < span; ++b)
-            for (int c = 0; c < span; ++c) {
-              int u[3] = {base[0] + a, base[1] + b, base[2] + c};
-              if (!inside(fd, u[0], u[1], u[2])) continue;
-              double wr = rweight(transfer, I, u);
-              if (wr == 0.0) continue;
-              long pu = pidx(fd, u[0], u[1], u[2]);
-              for (int e = 0; e < ns; ++e) {
-                int v[3] = {u[0] + off[3 * e], u[1] + off[3 * e + 1], u[2] + off[3 * e + 2]};
-                if (!inside(fd, v[0], v[1], v[2])) continue;
-                for (int ja = -2; ja <= 2; ++ja)
-                  for (int jb = -2; jb <= 2; ++jb)
-                    for (int jc = -2; jc <= 2; ++jc) {
-                      int J[3] = {I0 + ja, I1 + jb, I2 + jc};
-                      if (!inside(cd, J[0], J[1], J[2])) continue;
-                      double wp = pweight(transfer, v, J);
-                      if (wp == 0.0) continue;
-                      if (ja < -1 || ja > 1 || jb < -1 || jb > 1 || jc < -1 || jc > 1) return ORC_EINVAL;
-                      int o = (ja + 1) * 9 + (jb + 1) * 3 + (jc + 1);
-                      present[o] = 1;
-                      for (int r = 0; r < B; ++r)
-                        for (int cc = 0; cc < B; ++cc)
-                          Ac27[((Pc * 27 + o) * B + r) * B + cc] += wr * Af[((pu * ns + e) * B + r) * B + cc] * wp;
-                    }
-              }
-            }
+        int rc = rap_point(transfer, fd, cd, ns, off, B, Af, I, Ac27 + Pc * 27 * B * B, present);
+        if (rc) return rc;
       }
+  return ORC_OK;
+}
+
+/* The same chain sums for a list of coarse point indices only (for checking
+ * single entries of a large hierarchy): out27[t][27][B][B]. */
+int orc_rap27_at(int transfer, const int fd[3], int ns, const int* off, int B, const double* Af, long npoints,
+                 const long* points, double* out27) {
+  int cd[3], present[27];
+  orc_coarse_dims(fd, cd);
+  memset(out27, 0, sizeof(double) * npoints * 27 * B * B);
+  for (long t = 0; t < npoints; ++t) {
+    long P = points[t];
+    int I[3] = {(int)(P / ((long)cd[1] * cd[2])), (int)((P / cd[2]) % cd[1]), (int)(P % cd[2])};
+    int rc = rap_point(transfer, fd, cd, ns, off, B, Af, I, out27 + t * 27 * B * B, present);
+    if (rc) return rc;
+  }
   return ORC_OK;
 }
 

@@ -1,0 +1,591 @@
+// Point-parallel stencil kernels: SG-DIA SpMV / residual (Sec. 6.1.1), grid
+// transfers (Sec. 2 V-cycle; Table 3 patterns 3d27v and 3d8c), precision
+// casts and lowering, diagonal inverses and the dense coarsest level.
+#include "smg_internal.cuh"
+
+namespace {
+
+constexpr int TPB = 256;
+
+__device__ __forceinline__ bool inside3(int i, int j, int k, const Grid& g) {
+  return (unsigned)i < (unsigned)g.nx && (unsigned)j < (unsigned)g.ny && (unsigned)k < (unsigned)g.nz;
+}
+
+__device__ __forceinline__ void coords(long long p, const Grid& g, int& i, int& j, int& k) {
+  k = (int)(p % g.nz);
+  long long t = p / g.nz;
+  j = (int)(t % g.ny);
+  i = (int)(t / g.ny);
+}
+
+// ---------------------------------------------------------------------------
+// SpMV / residual.  One thread per point, all stencil entries unrolled
+// (NS known at compile time), one fused multiply-add per coefficient.
+// ---------------------------------------------------------------------------
+template <int PK, int NS>
+__global__ void __launch_bounds__(TPB) k_spmv1(Grid g, Stencil s, const typename Prec<PK>::val* __restrict__ A,
+                                               const float* __restrict__ scale,
+                                               const typename Prec<PK>::vec* __restrict__ x,
+                                               const typename Prec<PK>::vec* __restrict__ b,
+                                               typename Prec<PK>::vec* __restrict__ y, int mode) {
+  using V = typename Prec<PK>::vec;
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.n) return;
+  int i, j, k;
+  coords(p, g, i, j, k);
+  const typename Prec<PK>::val* a = A + p * NS;
+  V acc = 0;
+#pragma unroll
+  for (int e = 0; e < NS; ++e) {
+    int a0 = i + s.off[e][0], a1 = j + s.off[e][1], a2 = k + s.off[e][2];
+    V xv = inside3(a0, a1, a2, g) ? x[p + s.lin[e]] : V(0);
+    acc = fma((V)to_c(a[e]), xv, acc);
+  }
+  if (PK == KBF) acc = (V)scale[p] * acc;
+  y[p] = mode ? b[p] - acc : acc;
+}
+
+// Runtime stencil size (any mask).
+template <int PK>
+__global__ void __launch_bounds__(TPB) k_spmv1_any(Grid g, Stencil s, const typename Prec<PK>::val* __restrict__ A,
+                                                   const float* __restrict__ scale,
+                                                   const typename Prec<PK>::vec* __restrict__ x,
+                                                   const typename Prec<PK>::vec* __restrict__ b,
+                                                   typename Prec<PK>::vec* __restrict__ y, int mode) {
+  using V = typename Prec<PK>::vec;
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.n) return;
+  int i, j, k;
+  coords(p, g, i, j, k);
+  const typename Prec<PK>::val* a = A + p * s.ns;
+  V acc = 0;
+  for (int e = 0; e < s.ns; ++e) {
+    int a0 = i + s.off[e][0], a1 = j + s.off[e][1], a2 = k + s.off[e][2];
+    V xv = inside3(a0, a1, a2, g) ? x[p + s.lin[e]] : V(0);
+    acc = fma((V)to_c(a[e]), xv, acc);
+  }
+  if (PK == KBF) acc = (V)scale[p] * acc;
+  y[p] = mode ? b[p] - acc : acc;
+}
+
+// 3 unknowns per point, BxB blocks (FP64 or FP32 only).
+template <typename V>
+__global__ void __launch_bounds__(TPB) k_spmv3(Grid g, Stencil s, const V* __restrict__ A, const V* __restrict__ x,
+                                               const V* __restrict__ b, V* __restrict__ y, int mode) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.n) return;
+  int i, j, k;
+  coords(p, g, i, j, k);
+  V acc0 = 0, acc1 = 0, acc2 = 0;
+  for (int e = 0; e < s.ns; ++e) {
+    int a0 = i + s.off[e][0], a1 = j + s.off[e][1], a2 = k + s.off[e][2];
+    if (!inside3(a0, a1, a2, g)) continue;
+    const V* blk = A + (p * s.ns + e) * 9;
+    const V* xq = x + (p + s.lin[e]) * 3;
+    V x0 = xq[0], x1 = xq[1], x2 = xq[2];
+    acc0 = fma(blk[0], x0, fma(blk[1], x1, fma(blk[2], x2, acc0)));
+    acc1 = fma(blk[3], x0, fma(blk[4], x1, fma(blk[5], x2, acc1)));
+    acc2 = fma(blk[6], x0, fma(blk[7], x1, fma(blk[8], x2, acc2)));
+  }
+  if (mode) {
+    y[p * 3 + 0] = b[p * 3 + 0] - acc0;
+    y[p * 3 + 1] = b[p * 3 + 1] - acc1;
+    y[p * 3 + 2] = b[p * 3 + 2] - acc2;
+  } else {
+    y[p * 3 + 0] = acc0;
+    y[p * 3 + 1] = acc1;
+    y[p * 3 + 2] = acc2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Transfers.  Full weighting (3d27v): coarse I sits on fine 2I+1, 1-D weights
+// (1/2, 1, 1/2); R = P^T/8.  Piecewise constant (3d8c): R(I,u) = 1 on
+// u in 2I+{0,1}^3, P = R^T.  Fine points off the grid are skipped.
+// ---------------------------------------------------------------------------
+template <typename V, int B>
+__global__ void __launch_bounds__(TPB) k_restrict_fw(Grid f, Grid c, const V* __restrict__ rf, V* __restrict__ fc) {
+  long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (P >= c.n) return;
+  int I, J, K;
+  coords(P, c, I, J, K);
+  const V w1[3] = {V(0.5), V(1), V(0.5)};
+  V acc[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) acc[r] = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int u0 = 2 * I + a;
+    if (u0 >= f.nx) continue;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      int u1 = 2 * J + b;
+      if (u1 >= f.ny) continue;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        int u2 = 2 * K + cc;
+        if (u2 >= f.nz) continue;
+        V wgt = w1[a] * w1[b] * w1[cc] * V(0.125);
+        long long q = ((long long)u0 * f.ny + u1) * f.nz + u2;
+#pragma unroll
+        for (int r = 0; r < B; ++r) acc[r] = fma(wgt, rf[q * B + r], acc[r]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < B; ++r) fc[P * B + r] = acc[r];
+}
+
+template <typename V, int B>
+__global__ void __launch_bounds__(TPB) k_restrict_pc(Grid f, Grid c, const V* __restrict__ rf, V* __restrict__ fc) {
+  long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (P >= c.n) return;
+  int I, J, K;
+  coords(P, c, I, J, K);
+  V acc[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) acc[r] = 0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        long long q = ((long long)(2 * I + a) * f.ny + (2 * J + b)) * f.nz + (2 * K + cc);
+#pragma unroll
+        for (int r = 0; r < B; ++r) acc[r] += rf[q * B + r];
+      }
+#pragma unroll
+  for (int r = 0; r < B; ++r) fc[P * B + r] = acc[r];
+}
+
+// uf += P ec.  For full weighting, a fine coordinate v is either on a coarse
+// point (v odd: weight 1 from J = (v-1)/2) or between two (v even: weights
+// 1/2 from J = v/2 - 1 and J = v/2, the ones off the coarse grid dropped).
+template <typename V, int B>
+__global__ void __launch_bounds__(TPB) k_prolong_fw(Grid f, Grid c, const V* __restrict__ ec, V* __restrict__ uf) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= f.n) return;
+  int v0, v1, v2;
+  coords(q, f, v0, v1, v2);
+  int lo[3], cnt[3];
+  V w[3][2];
+  const int v[3] = {v0, v1, v2};
+  const int cn[3] = {c.nx, c.ny, c.nz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (v[d] & 1) {
+      lo[d] = (v[d] - 1) >> 1; cnt[d] = 1; w[d][0] = V(1); w[d][1] = V(0);
+    } else {
+      lo[d] = (v[d] >> 1) - 1; cnt[d] = 2; w[d][0] = V(0.5); w[d][1] = V(0.5);
+    }
+  }
+  V acc[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) acc[r] = 0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    int J0 = lo[0] + a;
+    if (a >= cnt[0] || (unsigned)J0 >= (unsigned)cn[0]) continue;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int J1 = lo[1] + b;
+      if (b >= cnt[1] || (unsigned)J1 >= (unsigned)cn[1]) continue;
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        int J2 = lo[2] + cc;
+        if (cc >= cnt[2] || (unsigned)J2 >= (unsigned)cn[2]) continue;
+        V wgt = w[0][a] * w[1][b] * w[2][cc];
+        long long P = ((long long)J0 * c.ny + J1) * c.nz + J2;
+#pragma unroll
+        for (int r = 0; r < B; ++r) acc[r] = fma(wgt, ec[P * B + r], acc[r]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < B; ++r) uf[q * B + r] += acc[r];
+}
+
+template <typename V, int B>
+__global__ void __launch_bounds__(TPB) k_prolong_pc(Grid f, Grid c, const V* __restrict__ ec, V* __restrict__ uf) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= f.n) return;
+  int v0, v1, v2;
+  coords(q, f, v0, v1, v2);
+  int J0 = v0 >> 1, J1 = v1 >> 1, J2 = v2 >> 1;
+  if (J0 >= c.nx || J1 >= c.ny || J2 >= c.nz) return;
+  long long P = ((long long)J0 * c.ny + J1) * c.nz + J2;
+#pragma unroll
+  for (int r = 0; r < B; ++r) uf[q * B + r] += ec[P * B + r];
+}
+
+__global__ void k_cast_d2f(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = (float)a[t];
+}
+__global__ void k_cast_f2d(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = (double)a[t];
+}
+
+// Off-grid coefficients must be exactly zero (SG-DIA zero padding).
+__global__ void k_check_padding(Grid g, Stencil s, int B, const double* __restrict__ A, int* count) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.n) return;
+  int i, j, k;
+  coords(p, g, i, j, k);
+  int bad = 0;
+  for (int e = 0; e < s.ns; ++e) {
+    if (inside3(i + s.off[e][0], j + s.off[e][1], k + s.off[e][2], g)) continue;
+    const double* blk = A + (p * s.ns + e) * B * B;
+    for (int t = 0; t < B * B; ++t) bad |= (blk[t] != 0.0);
+  }
+  if (bad) atomicAdd(count, 1);
+}
+
+// Lowered copy of a scalar matrix.  pk == K32: vals = (float)a.  pk == KBF:
+// scale_p = (float)max |a_pe| over all entries, vals = bf16 round-to-
+// nearest-even of a / scale_p computed in double; a zero row gets scale 1.
+// split != 0 (ILU factors): lower entries (e < ec) use their own scale
+// `scale`, centre and upper entries the scale `scale2` of the upper entries.
+__device__ __forceinline__ float row_scale(const double* a, int e0, int e1) {
+  double mx = 0.0;
+  for (int e = e0; e < e1; ++e) mx = fmax(mx, fabs(a[e]));
+  return mx > 0.0 ? (float)mx : 1.0f;
+}
+
+__global__ void k_lower(Grid g, Stencil s, const double* __restrict__ A, int pk, int split, void* vals, float* scale,
+                        float* scale2) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.n) return;
+  const double* a = A + p * s.ns;
+  if (pk == K32) {
+    float* v = (float*)vals + p * s.ns;
+    for (int e = 0; e < s.ns; ++e) v[e] = (float)a[e];
+    if (scale) scale[p] = 1.0f;
+    if (scale2) scale2[p] = 1.0f;
+    return;
+  }
+  __nv_bfloat16* v = (__nv_bfloat16*)vals + p * s.ns;
+  if (!split) {
+    const float sc = row_scale(a, 0, s.ns);
+    scale[p] = sc;
+    for (int e = 0; e < s.ns; ++e) v[e] = __double2bfloat16(a[e] / (double)sc);
+    return;
+  }
+  const float sl = row_scale(a, 0, s.ec), su = row_scale(a, s.ec + 1, s.ns);
+  scale[p] = sl;
+  scale2[p] = su;
+  for (int e = 0; e < s.ns; ++e) v[e] = __double2bfloat16(a[e] / (double)(e < s.ec ? sl : su));
+}
+
+// Stencil entries reordered: out[p][e] = in[p][perm[e]] (BxB blocks).
+__global__ void k_permute(long long n, int ns, int bb, const int* __restrict__ perm, const double* __restrict__ in,
+                          double* __restrict__ out) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = n * ns * bb;
+  if (t >= total) return;
+  long long p = t / (ns * bb);
+  int rem = (int)(t % (ns * bb));
+  int e = rem / bb, m = rem % bb;
+  out[t] = in[(p * ns + perm[e]) * bb + m];
+}
+
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = (float)a[t];
+}
+
+// Inverse of the diagonal coefficient (scalar) or of the 3x3 diagonal block
+// (Gauss-Jordan with partial pivoting on 3 rows).
+__global__ void k_diag_inverse(Grid g, Stencil s, int B, const double* __restrict__ A, double* __restrict__ dinv,
+                               int* err) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.n) return;
+  if (B == 1) {
+    double d = A[p * s.ns + s.ec];
+    if (d == 0.0) { atomicCAS(err, 0, SMG_EBREAKDOWN); dinv[p] = 0.0; return; }
+    dinv[p] = 1.0 / d;
+    return;
+  }
+  double W[3][6];
+  const double* D = A + (p * s.ns + s.ec) * 9;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 6; ++c) W[r][c] = c < 3 ? D[r * 3 + c] : (c - 3 == r ? 1.0 : 0.0);
+  for (int col = 0; col < 3; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 3; ++r)
+      if (fabs(W[r][col]) > fabs(W[piv][col])) piv = r;
+    if (W[piv][col] == 0.0) {
+      atomicCAS(err, 0, SMG_EBREAKDOWN);
+      for (int t = 0; t < 9; ++t) dinv[p * 9 + t] = 0.0;
+      return;
+    }
+    if (piv != col)
+      for (int c = 0; c < 6; ++c) { double t = W[col][c]; W[col][c] = W[piv][c]; W[piv][c] = t; }
+    double inv = 1.0 / W[col][col];
+    for (int c = 0; c < 6; ++c) W[col][c] *= inv;
+    for (int r = 0; r < 3; ++r) {
+      if (r == col) continue;
+      double f = W[r][col];
+      for (int c = 0; c < 6; ++c) W[r][c] -= f * W[col][c];
+    }
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) dinv[p * 9 + r * 3 + c] = W[r][3 + c];
+}
+
+// Dense (n*B)^2 row-major assembly of the coarsest stencil matrix.
+__global__ void k_assemble_dense(Grid g, Stencil s, int B, const double* __restrict__ A, double* __restrict__ M) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.n) return;
+  int i, j, k;
+  coords(p, g, i, j, k);
+  long long N = g.n * B;
+  for (int e = 0; e < s.ns; ++e) {
+    if (!inside3(i + s.off[e][0], j + s.off[e][1], k + s.off[e][2], g)) continue;
+    long long q = p + s.lin[e];
+    for (int r = 0; r < B; ++r)
+      for (int c = 0; c < B; ++c) M[(p * B + r) * N + q * B + c] = A[((p * s.ns + e) * B + r) * B + c];
+  }
+}
+
+// Gauss-Jordan elimination with partial pivoting on [M | I], one pivot column
+// per pair of launches: k_gj_pivot (one block) selects and swaps the pivot
+// row, scales it and saves column `col` of the other rows; k_gj_elim updates
+// every other row.
+__global__ void k_gj_pivot(int n, int col, double* M, double* Minv, double* colbuf, int* err) {
+  __shared__ double sv[1024];
+  __shared__ int si[1024];
+  int t = threadIdx.x;
+  double best = -1.0;
+  int bi = col;
+  for (int r = col + t; r < n; r += blockDim.x) {
+    double v = fabs(M[(long long)r * n + col]);
+    if (v > best) { best = v; bi = r; }
+  }
+  sv[t] = best;
+  si[t] = bi;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (t < h) {
+      if (sv[t + h] > sv[t] || (sv[t + h] == sv[t] && si[t + h] < si[t])) { sv[t] = sv[t + h]; si[t] = si[t + h]; }
+    }
+    __syncthreads();
+  }
+  int piv = si[0];
+  if (sv[0] <= 0.0) {
+    if (t == 0) atomicCAS(err, 0, SMG_EBREAKDOWN);
+    return;
+  }
+  if (piv != col) {
+    for (int c = t; c < n; c += blockDim.x) {
+      double a = M[(long long)col * n + c]; M[(long long)col * n + c] = M[(long long)piv * n + c];
+      M[(long long)piv * n + c] = a;
+      double b = Minv[(long long)col * n + c]; Minv[(long long)col * n + c] = Minv[(long long)piv * n + c];
+      Minv[(long long)piv * n + c] = b;
+    }
+  }
+  __syncthreads();
+  double inv = 1.0 / M[(long long)col * n + col];
+  __syncthreads();
+  for (int c = t; c < n; c += blockDim.x) {
+    M[(long long)col * n + c] *= inv;
+    Minv[(long long)col * n + c] *= inv;
+  }
+  for (int r = t; r < n; r += blockDim.x) colbuf[r] = (r == col) ? 0.0 : M[(long long)r * n + col];
+}
+
+__global__ void k_gj_elim(int n, int col, double* M, double* Minv, const double* colbuf, const int* err) {
+  if (*err) return;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)n * 2 * n;
+  if (idx >= total) return;
+  int r = (int)(idx / (2 * n));
+  int c = (int)(idx % (2 * n));
+  double f = colbuf[r];
+  if (f == 0.0) return;
+  if (c < n) {
+    if (c == col) { M[(long long)r * n + c] = 0.0; return; }
+    M[(long long)r * n + c] -= f * M[(long long)col * n + c];
+  } else {
+    c -= n;
+    Minv[(long long)r * n + c] -= f * Minv[(long long)col * n + c];
+  }
+}
+
+__global__ void k_set_identity(int n, double* Minv) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  Minv[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+}
+
+// y = Minv x: one warp per row, coalesced row reads, fixed-order shuffle sum.
+__global__ void k_dense_matvec(int n, const double* __restrict__ Minv, const double* __restrict__ x,
+                               double* __restrict__ y) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = Minv + (long long)warp * n;
+  double acc = 0.0;
+  for (int c = lane; c < n; c += 32) acc = fma(row[c], x[c], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[warp] = acc;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_spmv(const LevelView& L, const void* x, const void* b, void* y, int mode, cudaStream_t st) {
+  int nb = div_up(L.g.n, TPB);
+  if (L.B == 3) {
+    if (L.pk == K64)
+      k_spmv3<double><<<nb, TPB, 0, st>>>(L.g, L.s, (const double*)L.A, (const double*)x, (const double*)b,
+                                          (double*)y, mode);
+    else
+      k_spmv3<float><<<nb, TPB, 0, st>>>(L.g, L.s, (const float*)L.A, (const float*)x, (const float*)b, (float*)y,
+                                         mode);
+    return cudaGetLastError();
+  }
+#define SPMV_CASE(PK)                                                                                          \
+  {                                                                                                            \
+    using Val = typename Prec<PK>::val;                                                                        \
+    using Vec = typename Prec<PK>::vec;                                                                        \
+    if (L.s.ns == 27)                                                                                          \
+      k_spmv1<PK, 27><<<nb, TPB, 0, st>>>(L.g, L.s, (const Val*)L.A, L.scale, (const Vec*)x, (const Vec*)b,    \
+                                          (Vec*)y, mode);                                                      \
+    else if (L.s.ns == 7)                                                                                      \
+      k_spmv1<PK, 7><<<nb, TPB, 0, st>>>(L.g, L.s, (const Val*)L.A, L.scale, (const Vec*)x, (const Vec*)b,     \
+                                         (Vec*)y, mode);                                                       \
+    else                                                                                                       \
+      k_spmv1_any<PK><<<nb, TPB, 0, st>>>(L.g, L.s, (const Val*)L.A, L.scale, (const Vec*)x, (const Vec*)b,    \
+                                          (Vec*)y, mode);                                                      \
+  }
+  if (L.pk == K64) SPMV_CASE(K64)
+  else if (L.pk == K32) SPMV_CASE(K32)
+  else SPMV_CASE(KBF)
+#undef SPMV_CASE
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+static Grid coarse_of(Grid f) {
+  Grid c{f.nx / 2, f.ny / 2, f.nz / 2, 0};
+  c.n = (long long)c.nx * c.ny * c.nz;
+  return c;
+}
+
+cudaError_t launch_restrict(int transfer, Grid f, int B, int pk, const void* rf, void* fc, cudaStream_t st) {
+  Grid c = coarse_of(f);
+  int nb = div_up(c.n, TPB);
+  bool dbl = pk == K64;
+#define RCASE(V, BB)                                                                                   \
+  if (transfer == SMG_TRANSFER_FW27V)                                                                  \
+    k_restrict_fw<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)rf, (V*)fc);                              \
+  else                                                                                                 \
+    k_restrict_pc<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)rf, (V*)fc);
+  if (dbl) {
+    if (B == 1) { RCASE(double, 1) } else { RCASE(double, 3) }
+  } else {
+    if (B == 1) { RCASE(float, 1) } else { RCASE(float, 3) }
+  }
+#undef RCASE
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(int transfer, Grid f, int B, int pk, const void* ec, void* uf, cudaStream_t st) {
+  Grid c = coarse_of(f);
+  int nb = div_up(f.n, TPB);
+  bool dbl = pk == K64;
+#define PCASE(V, BB)                                                                                   \
+  if (transfer == SMG_TRANSFER_FW27V)                                                                  \
+    k_prolong_fw<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)ec, (V*)uf);                               \
+  else                                                                                                 \
+    k_prolong_pc<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)ec, (V*)uf);
+  if (dbl) {
+    if (B == 1) { PCASE(double, 1) } else { PCASE(double, 3) }
+  } else {
+    if (B == 1) { PCASE(float, 1) } else { PCASE(float, 3) }
+  }
+#undef PCASE
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_d2f(const double* a, float* b, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_cast_d2f<<<div_up(n, TPB), TPB, 0, st>>>(a, b, n);
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_cast_f2d(const float* a, double* b, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_cast_f2d<<<div_up(n, TPB), TPB, 0, st>>>(a, b, n);
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_padding(Grid g, const Stencil& s, int B, const double* A, int* count, cudaStream_t st) {
+  k_check_padding<<<div_up(g.n, TPB), TPB, 0, st>>>(g, s, B, A, count);
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lower_matrix(Grid g, const Stencil& s, const double* A, int pk, int split, void* vals, float* scale,
+                                float* scale2, cudaStream_t st) {
+  k_lower<<<div_up(g.n, TPB), TPB, 0, st>>>(g, s, A, pk, split, vals, scale, scale2);
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute(long long n, int ns, int bb, const int* perm, const double* in, double* out,
+                           cudaStream_t st) {
+  long long total = n * ns * bb;
+  if (total <= 0) return cudaSuccess;
+  k_permute<<<div_up(total, TPB), TPB, 0, st>>>(n, ns, bb, perm, in, out);
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_d2f_array(const double* a, float* b, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_d2f<<<div_up(n, TPB), TPB, 0, st>>>(a, b, n);
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_inverse(Grid g, const Stencil& s, int B, const double* A, double* dinv, int* err,
+                                cudaStream_t st) {
+  k_diag_inverse<<<div_up(g.n, TPB), TPB, 0, st>>>(g, s, B, A, dinv, err);
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_dense(Grid g, const Stencil& s, int B, const double* A, double* M, cudaStream_t st) {
+  long long N = g.n * B;
+  cudaError_t e = cudaMemsetAsync(M, 0, sizeof(double) * N * N, st);
+  if (e != cudaSuccess) return e;
+  k_assemble_dense<<<div_up(g.n, TPB), TPB, 0, st>>>(g, s, B, A, M);
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_jordan(int n, double* M, double* Minv, double* colbuf, int* err, cudaStream_t st) {
+  k_set_identity<<<div_up((long long)n * n, TPB), TPB, 0, st>>>(n, Minv);
+  int nb = div_up((long long)n * 2 * n, TPB);
+  for (int col = 0; col < n; ++col) {
+    k_gj_pivot<<<1, 1024, 0, st>>>(n, col, M, Minv, colbuf, err);
+    k_gj_elim<<<nb, TPB, 0, st>>>(n, col, M, Minv, colbuf, err);
+  }
+  smg_count_launch(1 + 2LL * n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_matvec(int n, const double* Minv, const double* x, double* y, cudaStream_t st) {
+  k_dense_matvec<<<div_up((long long)n * 32, TPB), TPB, 0, st>>>(n, Minv, x, y);
+  smg_count_launch(1);
+  return cudaGetLastError();
+}

@@ -73,14 +73,19 @@ def smoothed_field(shape, seed, sigma=4.0, std=1.5, trunc=3.0, device="cpu"):
     ker = ker / ker.sum()
     x = g
     for ax in range(3):
-        x = x.movedim(ax, -1)
-        sh = x.shape
-        y = x.reshape(-1, 1, sh[-1])
-        pad = min(r, sh[-1] - 1)
+        x = x.movedim(ax, -1).contiguous()
+        m = x.shape[-1]
+        pad = min(r, m - 1)
         kk = ker[r - pad:r + pad + 1] / ker[r - pad:r + pad + 1].sum()
-        y = torch.nn.functional.pad(y, (pad, pad), mode="reflect") if pad > 0 else y
-        y = torch.nn.functional.conv1d(y, kk.view(1, 1, -1))
-        x = y.reshape(sh).movedim(-1, ax)
+        if pad > 0:
+            # reflecting boundary without repeating the edge value
+            xp = torch.cat([x[..., 1:pad + 1].flip(-1), x, x[..., m - 1 - pad:m - 1].flip(-1)], dim=-1)
+        else:
+            xp = x
+        y = torch.zeros_like(x)
+        for t in range(2 * pad + 1):
+            y += kk[t] * xp[..., t:t + m]
+        x = y.movedim(-1, ax)
     x = x - x.mean()
     s = x.std()
     if s > 0:

@@ -1,0 +1,203 @@
+"""Python binding of the C ABI in include/smg.h (argument marshalling only).
+
+Every numerical step runs in libsmg.so's CUDA kernels.  PyTorch supplies
+device memory and streams: tensors are passed by ``data_ptr()`` and the
+current CUDA stream by its handle.  If the shared library has not been built,
+every call raises instead of falling back to anything else.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsmg.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENOTCONV, ENAN, ETIMEOUT = range(8)
+SGS, ILU0 = 0, 1
+FW27V, PC8C = 0, 1
+FP64, FP32, BF16 = 0, 1, 2
+PCG, FPCG, FGMRES = 0, 1, 2
+OP_SPMV, OP_RESIDUAL, OP_GS_FORWARD, OP_GS_BACKWARD, OP_GS_ZERO, OP_ILU_APPLY, OP_RESTRICT, OP_PROLONG_ADD, \
+    OP_COARSE_SOLVE, OP_ILU_LOWER, OP_ILU_UPPER = range(11)
+ARR_A, ARR_LU, ARR_DINV, ARR_AV, ARR_AS, ARR_LUV, ARR_LS, ARR_US, ARR_DINV32 = range(9)
+
+_lib = None
+
+
+class SmgError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s failed: %s (status %d)" % (what, strerror(status), status))
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("smoother", ctypes.c_int), ("transfer", ctypes.c_int), ("precision", ctypes.c_int),
+                ("krylov", ctypes.c_int), ("restart", ctypes.c_int), ("relax_w", ctypes.c_double),
+                ("max_levels", ctypes.c_int), ("spin_budget_ms", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("dims", (ctypes.c_int * 3) * 16), ("nstencil", ctypes.c_int * 16),
+                ("grid_complexity", ctypes.c_double), ("operator_complexity", ctypes.c_double),
+                ("vcycle_bytes", ctypes.c_double), ("vcycle_fp64_flops", ctypes.c_double),
+                ("setup_ms", ctypes.c_double), ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("transfer", ctypes.c_int), ("block", ctypes.c_int)]
+
+
+def lib():
+    """Load libsmg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsmg.so is not built; run __graft_entry__.build() or "
+                               "python paper_2506_21932_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double
+        L.smg_setup.argtypes = [ctypes.POINTER(vp), ip, i, ip, vp, i, ctypes.POINTER(Options), vp]
+        L.smg_vcycle.argtypes = [vp, vp, vp, vp]
+        L.smg_solve.argtypes = [vp, vp, vp, d, i, ip, ctypes.POINTER(d), vp]
+        L.smg_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.smg_destroy.argtypes = [vp]
+        L.smg_destroy.restype = None
+        L.smg_strerror.argtypes = [i]
+        L.smg_strerror.restype = ctypes.c_char_p
+        L.smg_level_count.argtypes = [vp]
+        L.smg_level_info.argtypes = [vp, i, ip, ip, ip]
+        L.smg_level_copy.argtypes = [vp, i, i, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), vp]
+        L.smg_level_apply.argtypes = [vp, i, i, vp, vp, vp, vp]
+        L.smg_derive_chains.argtypes = [i, i, ip, i, ip, i, ip, i, ip]
+        L.smg_version.restype = ctypes.c_char_p
+        L.smg_launch_count.restype = ctypes.c_longlong
+        L.smg_selftest_wait.argtypes = [vp, i, vp]
+        _lib = L
+    return _lib
+
+
+def launch_count():
+    """Kernels enqueued by libsmg.so since it was loaded."""
+    return int(lib().smg_launch_count())
+
+
+def strerror(status):
+    try:
+        return lib().smg_strerror(int(status)).decode()
+    except RuntimeError:
+        return "status %d" % status
+
+
+def _iarr(vals):
+    vals = [int(v) for v in vals]
+    return (ctypes.c_int * max(1, len(vals)))(*vals)
+
+
+def derive_chains(roff, aoff, poff, dim=3):
+    """Host-only symbolic chain derivation; returns a list of (r, a, q, dJ)."""
+    L = lib()
+    flat = lambda offs: _iarr([c for o in offs for c in (list(o) + [0] * (3 - len(o)))])
+    ro, ao, po = flat(roff), flat(aoff), flat(poff)
+    n = L.smg_derive_chains(dim, len(roff), ro, len(aoff), ao, len(poff), po, 0, None)
+    if n < 0:
+        raise ValueError("chain derivation failed")
+    buf = (ctypes.c_int * (5 * max(1, n)))()
+    L.smg_derive_chains(dim, len(roff), ro, len(aoff), ao, len(poff), po, n, buf)
+    return [tuple(buf[5 * t:5 * t + 4]) for t in range(n)]
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+class SMG:
+    """A structured-multigrid hierarchy living on the current CUDA device."""
+
+    def __init__(self, dims, offsets, coeffs, block=1, smoother=SGS, transfer=FW27V, precision=FP64,
+                 krylov=PCG, restart=30, relax_w=1.0, max_levels=0, spin_budget_ms=0, use_graph=0, stream=None):
+        import torch
+        if not (coeffs.is_cuda and coeffs.dtype == torch.float64 and coeffs.is_contiguous()):
+            raise ValueError("coeffs must be a contiguous float64 CUDA tensor")
+        self._lib = lib()
+        self.dims = tuple(int(t) for t in dims)
+        self.block = int(block)
+        self.n = self.dims[0] * self.dims[1] * self.dims[2]
+        self.precision = precision
+        opt = Options(smoother, transfer, precision, krylov, restart, relax_w, max_levels, spin_budget_ms, use_graph)
+        offs = [c for o in offsets for c in o]
+        h = ctypes.c_void_p()
+        rc = self._lib.smg_setup(ctypes.byref(h), _iarr(self.dims), len(offsets), _iarr(offs),
+                                 ctypes.c_void_p(coeffs.data_ptr()), self.block, ctypes.byref(opt), _stream(stream))
+        if rc != OK:
+            raise SmgError(rc, "smg_setup")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.smg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def vcycle(self, r, z, stream=None):
+        rc = self._lib.smg_vcycle(self.h, _ptr(r), _ptr(z), _stream(stream))
+        if rc != OK:
+            raise SmgError(rc, "smg_vcycle")
+
+    def solve(self, b, x, tol=1e-9, maxit=500, stream=None, check=True):
+        it, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+        rc = self._lib.smg_solve(self.h, _ptr(b), _ptr(x), tol, maxit, ctypes.byref(it), ctypes.byref(rr),
+                                 _stream(stream))
+        if check and rc != OK:
+            raise SmgError(rc, "smg_solve")
+        return it.value, rr.value, rc
+
+    def stats(self):
+        s = Stats()
+        rc = self._lib.smg_stats(self.h, ctypes.byref(s))
+        if rc != OK:
+            raise SmgError(rc, "smg_stats")
+        return {"levels": s.levels, "dims": [tuple(s.dims[l]) for l in range(s.levels)],
+                "nstencil": [s.nstencil[l] for l in range(s.levels)], "grid_complexity": s.grid_complexity,
+                "operator_complexity": s.operator_complexity, "vcycle_bytes": s.vcycle_bytes,
+                "vcycle_fp64_flops": s.vcycle_fp64_flops, "setup_ms": s.setup_ms}
+
+    @property
+    def nlevels(self):
+        return self._lib.smg_level_count(self.h)
+
+    def level_info(self, l):
+        d = (ctypes.c_int * 3)()
+        ns = ctypes.c_int()
+        off = (ctypes.c_int * 81)()
+        rc = self._lib.smg_level_info(self.h, l, d, ctypes.byref(ns), off)
+        if rc != OK:
+            raise SmgError(rc, "smg_level_info")
+        return tuple(d), [tuple(off[3 * e:3 * e + 3]) for e in range(ns.value)]
+
+    def level_array(self, l, which, stream=None):
+        """Copies a level array into a new uint8 CUDA tensor and returns it."""
+        import torch
+        need = ctypes.c_size_t(0)
+        rc = self._lib.smg_level_copy(self.h, l, which, None, 0, ctypes.byref(need), _stream(stream))
+        if rc != OK:
+            raise SmgError(rc, "smg_level_copy")
+        out = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+        rc = self._lib.smg_level_copy(self.h, l, which, ctypes.c_void_p(out.data_ptr()), need.value, None,
+                                      _stream(stream))
+        if rc != OK:
+            raise SmgError(rc, "smg_level_copy")
+        return out
+
+    def level_apply(self, l, op, x=None, b=None, y=None, stream=None):
+        rc = self._lib.smg_level_apply(self.h, l, op, _ptr(x), _ptr(b), _ptr(y), _stream(stream))
+        if rc != OK:
+            raise SmgError(rc, "smg_level_apply")
+
+    def selftest_wait(self, budget_ms=20, stream=None):
+        """Runs one bounded device wait that must time out; returns the status."""
+        return self._lib.smg_selftest_wait(self.h, budget_ms, _stream(stream))
