@@ -276,6 +276,10 @@ cudaError_t launch_wait_selftest(const int* flag, int* err, unsigned long long b
 cudaError_t launch_sweep(const LevelView& L, int kind, int dir, const void* M, const float* sc1, const float* sc2,
                          const void* dinv, double w, const void* b, void* u, SweepWs* ws, int* err,
                          const SweepCfg& cfg, cudaStream_t st) {
+  {
+    cudaError_t e2 = launch_sweep2(L, kind, dir, M, sc1, sc2, dinv, w, b, u, ws, err, cfg, st);
+    if (e2 != cudaErrorNotSupported) return e2;
+  }
   SweepParams P;
   P.g = L.g;
   P.s = L.s;

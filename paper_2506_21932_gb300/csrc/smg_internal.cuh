@@ -166,6 +166,13 @@ cudaError_t launch_sweep(const LevelView& L, int kind, int dir, const void* M, c
                          const void* dinv, double w, const void* b, void* u, SweepWs* ws, int* err,
                          const SweepCfg& cfg, cudaStream_t st);
 
+// Software-pipelined variant for the lexicographic 7/19/27-point masks with
+// one unknown per point; returns cudaErrorNotSupported (nothing launched) for
+// any other level, which launch_sweep then runs with the generic kernel.
+cudaError_t launch_sweep2(const LevelView& L, int kind, int dir, const void* M, const float* sc1, const float* sc2,
+                          const void* dinv, double w, const void* b, void* u, SweepWs* ws, int* err,
+                          const SweepCfg& cfg, cudaStream_t st);
+
 // Bounded wait on a flag nobody sets (failure-path self-test).
 cudaError_t launch_wait_selftest(const int* flag, int* err, unsigned long long budget_ns, cudaStream_t st);
 
