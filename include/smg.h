@@ -211,6 +211,42 @@ int smg_selftest_wait(smg_t h, int budget_ms, void* stream);
 int smg_derive_chains(int dim, int nr, const int* roff, int na, const int* aoff, int np, const int* poff,
                       int max_chains, int* chains);
 
+/* ---------------------------------------------------------------------------
+ * One Gauss-Seidel or ILU(0) triangular sweep that allocates no memory.
+ * No counterpart in the paper: it exists for callers that cannot let a
+ * library allocate device memory -- applications that own every byte of the
+ * GPU through their own pool, fixed-budget real-time or embedded callers,
+ * plug-ins whose host forbids cudaMalloc (it synchronises the device and
+ * fragments the host's pool).  It needs no context: the caller passes the
+ * matrix and vectors, and the sweep's scratch (per-plane progress counters,
+ * plane ticket, error word: about 16 KB) is a fixed array in device memory
+ * that every GPU which loads this library keeps until the process exits.
+ *  op        SMG_OP_GS_FORWARD / SMG_OP_GS_BACKWARD / SMG_OP_GS_ZERO (u is
+ *            the iterate, updated in place, b the right-hand side, dinv the
+ *            inverse diagonal 1/a_pp), SMG_OP_ILU_LOWER (u = L^{-1} b, M the
+ *            ILU(0) factors of smg_level_copy which 1, dinv unused, u may
+ *            equal b), SMG_OP_ILU_UPPER (u = U^{-1} b, dinv = 1/u_pp, u may
+ *            equal b).  The results equal smg_level_apply's for the same op.
+ *  dims      host int[3]; nx <= 4096 (the scratch holds one counter per
+ *            x-plane), ny <= 1024, nz <= 4096.
+ *  nstencil, offsets  host; offsets in lexicographic order (dx slowest),
+ *            unique, symmetric, with the centre (no reordered copy is made).
+ *  M, dinv, b, u  device double, one value per point, layouts as above.
+ *  relax_w   GS weight in (0, 2); 0 means 1.  spin_budget_ms: bound on any
+ *            device-side wait (<= 0 means 1000).
+ * FP64, one unknown per point.  The first call on a device looks up the
+ * scratch's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before capturing a stream.  All calls share the scratch and
+ * each clears the part that must start at zero, so two calls that overlap
+ * on the GPU (different streams, or threads without ordering) race and must
+ * not be issued.  Calls no allocating routine.  Synchronises the stream.
+ * Errors: SMG_EINVAL (sizes beyond the limits above, unsorted or invalid
+ * offsets, bad op or pointers), SMG_ECUDA, SMG_ETIMEOUT.
+ * ------------------------------------------------------------------------- */
+int smg_sweep_noalloc(int op, const int dims[3], int nstencil, const int* offsets, const double* M,
+                      const double* dinv, const double* b, double* u, double relax_w, int spin_budget_ms,
+                      void* stream);
+
 /* Library version string. */
 const char* smg_version(void);
 

@@ -68,8 +68,18 @@ def lib():
         L.smg_version.restype = ctypes.c_char_p
         L.smg_launch_count.restype = ctypes.c_longlong
         L.smg_selftest_wait.argtypes = [vp, i, vp]
+        L.smg_sweep_noalloc.argtypes = [i, ip, i, ip, vp, vp, vp, vp, d, i, vp]
         _lib = L
     return _lib
+
+
+def sweep_noalloc(op, dims, offsets, M, dinv, b, u, relax_w=1.0, spin_budget_ms=0, stream=None):
+    """One GS or ILU(0) sweep through smg_sweep_noalloc, the entry point that
+    allocates no device memory (for callers whose device memory is owned by
+    someone else).  Tensors are float64 CUDA tensors; returns the status."""
+    flat = [c for o in offsets for c in o]
+    return lib().smg_sweep_noalloc(op, _iarr(dims), len(offsets), _iarr(flat), _ptr(M), _ptr(dinv), _ptr(b),
+                                   _ptr(u), relax_w, spin_budget_ms, _stream(stream))
 
 
 def launch_count():
