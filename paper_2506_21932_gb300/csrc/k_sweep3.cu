@@ -1,0 +1,475 @@
+// Warp-pipelined wavefront sweeps (exact lexicographic order) for the
+// 7/19/27-point masks with one unknown per point.
+//
+// Same global schedule as k_sweep.cu / k_sweep2.cu: point (i,j,k) runs at
+// t = SA*i + SB*j + k.  What changes is who waits for whom:
+//  * A CTA owns W consecutive x-planes.  Each plane is split into warps of
+//    32 y-columns; every warp runs its own time loop.  A warp may run local
+//    step s once its left neighbour warp has finished step s-1 and the
+//    previous plane has finished global time t+1 (its values two steps ahead
+//    are loaded early).  These conditions are read from per-warp progress
+//    counters in shared memory (CTA-scope acquire/release), so no CTA-wide
+//    barrier is taken per step and a slow warp only delays the warps that
+//    really depend on it.
+//  * One extra warp talks to the other CTAs: it publishes the progress of
+//    the CTA's last plane with GPU-scope release stores and polls the
+//    previous CTA's progress (relaxed loads, one acquire fence per new
+//    value), forwarding it into shared memory.  Compute warps never execute
+//    a GPU-scope fence.
+// Inside a warp the step body is the software pipeline of k_sweep2.cu:
+// finish point k from a partial sum prepared one step earlier plus the own
+// column (register) and neighbour column (shared ring) terms of the previous
+// step; pre-sum point k+1 from operands loaded one step earlier; load the
+// operands of point k+2.  Every wait is bounded.
+#include <climits>
+
+#include "smg_internal.cuh"
+
+namespace {
+
+template <int NS> struct Shape;
+template <> struct Shape<27> {
+  static constexpr int SA = 4, SB = 2, EC = 13;
+  __host__ __device__ static constexpr int o(int e, int d) {
+    return d == 0 ? e / 9 - 1 : (d == 1 ? (e / 3) % 3 - 1 : e % 3 - 1);
+  }
+};
+template <> struct Shape<7> {
+  static constexpr int SA = 1, SB = 1, EC = 3;
+  __host__ __device__ static constexpr int o(int e, int d) {
+    return d == 0 ? (e == 0 ? -1 : (e == 6 ? 1 : 0)) : d == 1 ? (e == 1 ? -1 : (e == 5 ? 1 : 0))
+                                                               : (e == 2 ? -1 : (e == 4 ? 1 : 0));
+  }
+};
+template <> struct Shape<19> {
+  static constexpr int SA = 3, SB = 2, EC = 9;
+  __host__ __device__ static constexpr int o(int e, int d) {
+    constexpr int t[19][3] = {{-1, -1, 0}, {-1, 0, -1}, {-1, 0, 0}, {-1, 0, 1}, {-1, 1, 0}, {0, -1, -1}, {0, -1, 0},
+                              {0, -1, 1},  {0, 0, -1},  {0, 0, 0},  {0, 0, 1},  {0, 1, -1}, {0, 1, 0},   {0, 1, 1},
+                              {1, -1, 0},  {1, 0, -1},  {1, 0, 0},  {1, 0, 1},  {1, 1, 0}};
+    return t[e][d];
+  }
+};
+
+enum { C_SKIP = 0, C_OWN = 1, C_LATE = 2, C_EARLY = 3, C_MEM = 4 };
+
+template <int NS, int KIND, int DIR>
+__host__ __device__ constexpr int cls(int e) {
+  using S = Shape<NS>;
+  const int sx = DIR * S::o(e, 0), sy = DIR * S::o(e, 1), sz = DIR * S::o(e, 2);
+  if (e == S::EC) return C_SKIP;
+  const bool is_new = sx < 0 || (sx == 0 && (sy < 0 || (sy == 0 && sz < 0)));
+  if (!(KIND == SW_GS_FULL || is_new)) return C_SKIP;
+  if (sx == 0 && sy == 0 && sz == -1) return C_OWN;
+  if (sx == 0 && sy == -1) return sz == S::SB - 1 ? C_LATE : C_EARLY;
+  return C_MEM;
+}
+
+struct Sweep3Params {
+  Grid g;
+  unsigned long long budget_ns;
+  const void* M;
+  const float* scale;
+  const void* dinv;
+  double w;
+  const void* b;  // may alias u
+  void* u;
+  SweepWs* ws;    // prog[] indexed by plane group
+  int* err;
+  int lin[27];
+};
+
+constexpr int kMaxWarpsPerPlane = 16;  // ny <= 512
+constexpr int kMaxThreads = 544;       // 17 warps: keeps 120 registers per thread
+constexpr int kPrefetch = 10;
+constexpr int kDone = INT_MAX / 2;
+// Shared ring of the last kRing values of every column.  A column's value
+// at point k is overwritten by point k + kRing, so a warp may run at most
+// kRing - SB - 2 steps ahead of its right-hand neighbour, which still has
+// to read the left column's values down to its point k - 1.
+constexpr int kRing = 8;
+
+__device__ __forceinline__ int ld_acq_cta(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel_cta(int* p, int v) {
+  asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+template <int W>
+struct Shared3 {
+  int wdone[W][kMaxWarpsPerPlane];  // per compute warp: all local steps < value are finished
+  int avail;                        // previous CTA's last plane: global time up to which it is finished
+  int abort;
+  int group;
+};
+
+// FP64 sweeps that use every stencil entry hold twice the operands of the
+// others; they get 9 warps (ny <= 256) and the registers that leaves.
+template <int PK, int KIND>
+__host__ __device__ constexpr int max_threads() {
+  return (PK == K64 && KIND == SW_GS_FULL) ? 288 : kMaxThreads;
+}
+
+template <int PK, int NS, int KIND, int DIR, int W>
+__global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Params P) {
+  using V = typename Prec<PK>::vec;
+  using Val = typename Prec<PK>::val;
+  using S = Shape<NS>;
+  constexpr int SA = S::SA, SB = S::SB;
+  extern __shared__ unsigned char dyn_smem[];
+  __shared__ Shared3<W> sh;
+
+  const Grid g = P.g;
+  const int NW = (g.ny + 31) >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ncompute = W * NW;
+  const bool comm = warp == ncompute;
+  constexpr int LEAD = kRing - SB - 2;  // largest lead over the right-hand warp
+  // shared value ring: hist[plane][k % kRing][column]
+  V* hist = (V*)dyn_smem;
+  const int ngroups = (g.nx + W - 1) / W;
+
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      sh.group = atomicAdd(&P.ws->ticket, 1);
+      sh.abort = 0;
+      sh.avail = 0;
+    }
+    __syncthreads();
+    const int I = sh.group;
+    if (I >= ngroups) break;
+    const int nplanes = min(W, g.nx - I * W);
+    if (threadIdx.x < W * kMaxWarpsPerPlane) {
+      const int p = threadIdx.x / kMaxWarpsPerPlane, w = threadIdx.x % kMaxWarpsPerPlane;
+      // a warp has trivially finished every step before its first one
+      sh.wdone[p][w] = (p < nplanes && w < NW) ? SB * 32 * w - 2 : kDone;
+    }
+    if (threadIdx.x == 0 && I == 0) sh.avail = kDone;
+    __syncthreads();
+
+    if (comm) {
+      // ---- communication warp: publish the last plane, poll the previous CTA
+      if (lane == 0) {
+        const int plast = nplanes - 1;
+        const int gt0 = SA * (I * W + plast);
+        int published = INT_MIN, seen = (I == 0) ? kDone : 0;
+        unsigned long long t_wait = 0;
+        for (;;) {
+          int T = kDone;
+          for (int w = 0; w < NW; ++w) T = min(T, ld_acq_cta(&sh.wdone[plast][w]));
+          if (T != published) {
+            st_release(&P.ws->prog[I], T >= kDone ? kDone : gt0 + T);
+            published = T;
+          }
+          if (T >= kDone) break;
+          if (I > 0 && seen < kDone) {
+            const int v = ld_relaxed(&P.ws->prog[I - 1]);
+            if (v > seen) {
+              __threadfence();
+              seen = v;
+              st_rel_cta(&sh.avail, v);
+              t_wait = 0;
+            } else {
+              // bounded: the previous CTA must make progress within the budget
+              const unsigned long long now = globaltimer_ns();
+              if (t_wait == 0) t_wait = now;
+              else if (now - t_wait > P.budget_ns) {
+                atomicCAS(P.err, 0, DEV_ERR_TIMEOUT);
+                st_rel_cta(&sh.abort, 1);
+                st_release(&P.ws->prog[I], kDone);
+                break;
+              }
+            }
+          }
+          if (ld_relaxed(P.err) != 0) {
+            st_rel_cta(&sh.abort, 1);
+            st_release(&P.ws->prog[I], kDone);
+            break;
+          }
+        }
+      }
+    } else if (warp < W * NW) {
+      // ---- compute warp (p, w)
+      const int p = warp / NW, w = warp % NW;
+      if (p < nplanes) {
+        const Val* __restrict__ M = (const Val*)P.M;
+        const V* b = (const V*)P.b;
+        V* u = (V*)P.u;
+        const V* __restrict__ dinv = (const V*)P.dinv;
+        const bool relax = P.w != 1.0;
+        const V wv = (V)P.w;
+        const int Ip = I * W + p;  // schedule plane
+        const int i = DIR > 0 ? Ip : g.nx - 1 - Ip;
+        const int J = 32 * w + lane;
+        const bool colok = J < g.ny;
+        const int j = DIR > 0 ? J : g.ny - 1 - J;
+        const int jlast = min(32 * w + 31, g.ny - 1);
+        const int s_begin = SB * 32 * w - 2;
+        const int s_end = SB * jlast + g.nz - 1;
+        const int gt0 = SA * Ip;
+        V* hp = hist + (size_t)p * kRing * (NW * 32);
+        int have_left = (w == 0) ? kDone : INT_MIN;        // cached progress of the left warp
+        int have_right = (w + 1 == NW) ? kDone : INT_MIN;  // cached progress of the right warp
+        int have_up = INT_MIN;                             // cached progress of the previous plane
+        Val cB[NS];
+        V mB[NS];
+        V bB = V(0), dB = V(0), uoB = V(0);
+        float sB = 1.0f;
+        V accA = V(0), bA = V(0), dA = V(0), uoA = V(0);
+        Val cOwnA = Val(0), cLateA = Val(0);
+        float sA = 1.0f;
+        V carry = V(0);
+#pragma unroll
+        for (int e = 0; e < NS; ++e) {
+          cB[e] = Val(0);
+          mB[e] = V(0);
+        }
+        bool aborted = false;
+        for (int s = s_begin; s <= s_end; ++s) {
+          // -- dependencies, checked by lane 0 against cached counters
+          if (lane == 0) {
+            unsigned long long t_start = 0;
+            for (;;) {
+              bool ok = true;
+              if (have_left < s) {
+                have_left = ld_acq_cta(&sh.wdone[p][w - 1]);
+                ok = have_left >= s;
+              }
+              if (ok && have_right < s - LEAD) {
+                have_right = ld_acq_cta(&sh.wdone[p][w + 1]);
+                ok = have_right >= s - LEAD;
+              }
+              if (ok) {
+                if (p == 0) {
+                  if (have_up < gt0 + s + 2) {
+                    have_up = ld_acq_cta(&sh.avail);
+                    ok = have_up >= gt0 + s + 2;
+                  }
+                } else if (have_up < s + SA + 2) {
+                  int T = kDone;
+                  for (int ww = 0; ww < NW; ++ww) T = min(T, ld_acq_cta(&sh.wdone[p - 1][ww]));
+                  have_up = T;
+                  ok = have_up >= s + SA + 2;
+                }
+              }
+              if (ok) break;
+              if (ld_acq_cta(&sh.abort)) { aborted = true; break; }
+              const unsigned long long now = globaltimer_ns();
+              if (t_start == 0) t_start = now;
+              else if (now - t_start > P.budget_ns) {
+                atomicCAS(P.err, 0, DEV_ERR_TIMEOUT);
+                st_rel_cta(&sh.abort, 1);
+                aborted = true;
+                break;
+              }
+            }
+          }
+          aborted = __shfl_sync(0xffffffffu, aborted, 0);
+          if (aborted) break;
+          __syncwarp();
+          const int K = s - SB * J;
+
+          // (1) finish point K
+          if (colok && K >= 0 && K < g.nz) {
+            V sacc = accA;
+#pragma unroll
+            for (int e = 0; e < NS; ++e) {
+              if (cls<NS, KIND, DIR>(e) == C_OWN) sacc = fma((V)to_c(cOwnA), carry, sacc);
+              if (cls<NS, KIND, DIR>(e) == C_LATE) {
+                const int kk = K + DIR * S::o(e, 2);
+                const V v = (J > 0 && kk >= 0 && kk < g.nz) ? hp[(kk & (kRing - 1)) * (NW * 32) + J - 1] : V(0);
+                sacc = fma((V)to_c(cLateA), v, sacc);
+              }
+            }
+            if (PK == KBF) sacc = (V)sA * sacc;
+            V r;
+            if (KIND == SW_ILU_L) {
+              r = bA - sacc;
+            } else {
+              r = (bA - sacc) * dA;
+              if (KIND != SW_ILU_U && relax) r = (KIND == SW_GS_ZERO) ? wv * r : (V(1) - wv) * uoA + wv * r;
+            }
+            const int k = DIR > 0 ? K : g.nz - 1 - K;
+            u[((long long)i * g.ny + j) * g.nz + k] = r;
+            hp[(K & (kRing - 1)) * (NW * 32) + J] = r;
+            carry = r;
+          }
+
+          // (2) partial sum of point K+1
+          const int K1 = K + 1;
+          if (colok && K1 >= 0 && K1 < g.nz) {
+            V a0 = V(0), a1 = V(0), a2 = V(0), a3 = V(0);
+            int q = 0;
+#pragma unroll
+            for (int e = 0; e < NS; ++e) {
+              const int c = cls<NS, KIND, DIR>(e);
+              V tv = V(0);
+              bool has = false;
+              if (c == C_MEM) {
+                tv = mB[e];
+                has = true;
+              } else if (c == C_EARLY) {
+                const int kk = K1 + DIR * S::o(e, 2);
+                tv = (J > 0 && kk >= 0 && kk < g.nz) ? hp[(kk & (kRing - 1)) * (NW * 32) + J - 1] : V(0);
+                has = true;
+              }
+              if (has) {
+                const V cv = (V)to_c(cB[e]);
+                if ((q & 3) == 0) a0 = fma(cv, tv, a0);
+                else if ((q & 3) == 1) a1 = fma(cv, tv, a1);
+                else if ((q & 3) == 2) a2 = fma(cv, tv, a2);
+                else a3 = fma(cv, tv, a3);
+                ++q;
+              }
+              if (c == C_OWN) cOwnA = cB[e];
+              if (c == C_LATE) cLateA = cB[e];
+            }
+            accA = (a0 + a1) + (a2 + a3);
+            bA = bB;
+            dA = dB;
+            sA = sB;
+            uoA = uoB;
+          }
+
+          // (3) loads of point K+2
+          const int K2 = K + 2;
+          if (colok && K2 >= 0 && K2 < g.nz) {
+            const int k2 = DIR > 0 ? K2 : g.nz - 1 - K2;
+            const long long p2 = ((long long)i * g.ny + j) * g.nz + k2;
+            const Val* a = M + p2 * NS;
+#pragma unroll
+            for (int e = 0; e < NS; ++e) {
+              const int c = cls<NS, KIND, DIR>(e);
+              if (c != C_SKIP) cB[e] = a[e];
+              if (c == C_MEM) {
+                const int ox = S::o(e, 0), oy = S::o(e, 1), oz = S::o(e, 2);
+                const bool in = (unsigned)(i + ox) < (unsigned)g.nx && (unsigned)(j + oy) < (unsigned)g.ny &&
+                                (unsigned)(k2 + oz) < (unsigned)g.nz;
+                V v = V(0);
+                if (in) {
+                  // the previous schedule plane of another CTA: read through L2;
+                  // everything else (this CTA's planes, old values) through L1
+                  const bool other_cta = (DIR * ox < 0) && p == 0;
+                  v = other_cta ? __ldcg(u + p2 + P.lin[e]) : u[p2 + P.lin[e]];
+                }
+                mB[e] = v;
+              }
+            }
+            bB = b[p2];
+            if (KIND != SW_ILU_L) dB = dinv[p2];
+            if (PK == KBF) sB = P.scale[p2];
+            if (KIND == SW_GS_FULL && relax) uoB = u[p2];
+            if (K2 + kPrefetch < g.nz) {
+              const char* pf = (const char*)(M + (p2 + DIR * kPrefetch) * NS);
+              prefetch_l2(pf);
+              if (NS * sizeof(Val) > 128) prefetch_l2(pf + 128);
+            }
+          }
+          // -- this warp has finished step s
+          __syncwarp();
+          if (lane == 0) st_rel_cta(&sh.wdone[p][w], s + 1);
+        }
+        if (lane == 0) st_rel_cta(&sh.wdone[p][w], kDone);
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    sh.group = (atomicAdd(&P.ws->finished, 1) == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  if (sh.group) {
+    for (int q = threadIdx.x; q < ngroups; q += blockDim.x) P.ws->prog[q] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      P.ws->ticket = 0;
+      __threadfence();
+      P.ws->finished = 0;
+    }
+  }
+}
+
+template <int NS>
+bool canonical(const Stencil& s) {
+  if (s.ns != NS) return false;
+  for (int e = 0; e < NS; ++e)
+    for (int d = 0; d < 3; ++d)
+      if (s.off[e][d] != Shape<NS>::o(e, d)) return false;
+  return true;
+}
+
+template <int PK, int NS, int W>
+cudaError_t launch_kind(int kind, int dir, const Sweep3Params& P, cudaStream_t st) {
+  using V = typename Prec<PK>::vec;
+  const int NW = (P.g.ny + 31) / 32;
+  const int nthr = (W * NW + 1) * 32;
+  const size_t smem = sizeof(V) * kRing * (size_t)(NW * 32) * W;  // <= 64 KB for ny <= 512
+  const int grid = (P.g.nx + W - 1) / W;
+  auto go = [&](auto kern) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, nthr, smem, st>>>(P);
+    return cudaGetLastError();
+  };
+  if (kind == SW_GS_ZERO) return go(k_sweep3<PK, NS, SW_GS_ZERO, 1, W>);
+  if (kind == SW_ILU_L) return go(k_sweep3<PK, NS, SW_ILU_L, 1, W>);
+  if (kind == SW_ILU_U) return go(k_sweep3<PK, NS, SW_ILU_U, -1, W>);
+  if (dir > 0) return go(k_sweep3<PK, NS, SW_GS_FULL, 1, W>);
+  return go(k_sweep3<PK, NS, SW_GS_FULL, -1, W>);
+}
+
+}  // namespace
+
+// Planes per CTA: FP64 sweeps are bound by the FP64 pipe, so one plane per
+// CTA keeps the per-SM work at one plane; FP32 / BF16 sweeps are bound by
+// synchronisation latency, so two planes share a CTA and every other plane
+// hand-off stays inside the SM.
+cudaError_t launch_sweep3(const LevelView& L, int kind, int dir, const void* M, const float* sc1, const float* sc2,
+                          const void* dinv, double w, const void* b, void* u, SweepWs* ws, int* err,
+                          const SweepCfg& cfg, cudaStream_t st) {
+  const int ns = L.s.ns;
+  if (L.B != 1) return cudaErrorNotSupported;
+  if (!((ns == 27 && canonical<27>(L.s)) || (ns == 7 && canonical<7>(L.s)) || (ns == 19 && canonical<19>(L.s))))
+    return cudaErrorNotSupported;
+  const int NW = (L.g.ny + 31) / 32;
+  const int W = (L.pk != K64 && (2 * NW + 1) * 32 <= kMaxThreads) ? 2 : 1;
+  const int maxt = (L.pk == K64 && kind == SW_GS_FULL) ? max_threads<K64, SW_GS_FULL>() : kMaxThreads;
+  if (NW > kMaxWarpsPerPlane || (W * NW + 1) * 32 > maxt) return cudaErrorNotSupported;
+  Sweep3Params P;
+  P.g = L.g;
+  P.budget_ns = cfg.budget_ns;
+  P.M = M;
+  P.scale = kind == SW_ILU_U ? sc2 : sc1;
+  P.dinv = dinv;
+  P.w = w;
+  P.b = b;
+  P.u = u;
+  P.ws = ws;
+  P.err = err;
+  for (int e = 0; e < 27; ++e) P.lin[e] = L.s.lin[e];
+  cudaError_t e;
+#define DISPATCH(PK, WW)                                                   \
+  do {                                                                     \
+    if (ns == 27) e = launch_kind<PK, 27, WW>(kind, dir, P, st);           \
+    else if (ns == 7) e = launch_kind<PK, 7, WW>(kind, dir, P, st);        \
+    else e = launch_kind<PK, 19, WW>(kind, dir, P, st);                    \
+  } while (0)
+  if (L.pk == K64) DISPATCH(K64, 1);
+  else if (L.pk == K32) {
+    if (W == 2) DISPATCH(K32, 2);
+    else DISPATCH(K32, 1);
+  } else {
+    if (W == 2) DISPATCH(KBF, 2);
+    else DISPATCH(KBF, 1);
+  }
+#undef DISPATCH
+  smg_count_launch(1);
+  return e;
+}

@@ -100,7 +100,8 @@ def test_spmv_and_residual(S, orc, d, off, B):
 
 
 @pytest.mark.parametrize("d,off", [((5, 6, 7), I.OFF27), ((9, 7, 11), I.OFF7), ((6, 9, 5), I.OFF19),
-                                   ((1, 1, 13), I.OFF7), ((3, 1, 8), I.OFF27), ((8, 33, 6), I.OFF27)])
+                                   ((1, 1, 13), I.OFF7), ((3, 1, 8), I.OFF27), ((8, 33, 6), I.OFF27),
+                                   ((6, 130, 9), I.OFF27), ((5, 97, 7), I.OFF7), ((4, 200, 3), I.OFF19)])
 def test_gs_sweeps_exact_order(S, orc, d, off):
     """Forward, backward and zero-guess sweeps reproduce the sequential
     lexicographic Gauss-Seidel (ragged grids, ny above one warp, 1-wide)."""
@@ -338,9 +339,10 @@ def test_lowered_arrays_bit_exact(S, orc, smoother):
         assert np.mean(lv == want) > 0.999
 
 
-@pytest.mark.parametrize("prec,smoother", [(1, 0), (1, 1), (2, 0), (2, 1)])
-def test_low_precision_vcycle(S, orc, prec, smoother):
-    d = (32, 32, 32)
+@pytest.mark.parametrize("prec,smoother,d", [(1, 0, (32, 32, 32)), (1, 1, (32, 32, 32)), (2, 0, (32, 32, 32)),
+                                             (2, 1, (32, 32, 32)), (1, 1, (16, 96, 24)), (2, 0, (24, 160, 16)),
+                                             (1, 0, (10, 288, 8))])
+def test_low_precision_vcycle(S, orc, prec, smoother, d):
     off, A = problem("q1", d, 2)
     r = I.rhs(np.prod(d), 5).numpy()
     h = make(S, d, off, A, smoother=smoother, precision=prec)
