@@ -188,3 +188,27 @@ def block7_layered(dims, seed, layer=8, lo=1e-3, hi=1e3, device="cpu"):
     A = S.view(-1, 7, 1, 1) * I3.view(1, 1, 3, 3)
     A[:, 3] = S[:, 3].view(-1, 1, 1) * (I3 + C).view(1, 3, 3)
     return A.contiguous()
+
+
+# The learned post-smoother's network: channel counts per layer and the size
+# of its parameter vector (per layer W[cout][cin][3][3][3] followed by b[cout]).
+CNN_CHANNELS = (2, 16, 16, 1)
+CNN_PARAMS = sum(co * ci * 27 + co for ci, co in zip(CNN_CHANNELS[:-1], CNN_CHANNELS[1:]))
+
+
+def cnn_theta(seed):
+    """Seeded initial parameters of the post-smoother network (FP32, flat):
+    weights uniform on +-sqrt(6 / (27 cin)) (He-uniform), biases zero."""
+    g = _gen(seed)
+    parts = []
+    for ci, co in zip(CNN_CHANNELS[:-1], CNN_CHANNELS[1:]):
+        lim = math.sqrt(6.0 / (27 * ci))
+        parts.append((torch.rand(co * ci * 27, generator=g, dtype=torch.float64) * 2.0 - 1.0) * lim)
+        parts.append(torch.zeros(co, dtype=torch.float64))
+    return torch.cat(parts).to(torch.float32)
+
+
+def cnn_volume(dims, channels, seed, scale=1.0):
+    """Seeded FP32 volume [channels][nx*ny*nz] with iid normal entries."""
+    n = int(dims[0]) * int(dims[1]) * int(dims[2])
+    return (torch.randn(channels, n, generator=_gen(seed), dtype=torch.float64) * scale).to(torch.float32)
