@@ -5,22 +5,28 @@
 // t = SA*i + SB*j + k.  What changes is who waits for whom:
 //  * A CTA owns W consecutive x-planes.  Each plane is split into warps of
 //    32 y-columns; every warp runs its own time loop.  A warp may run local
-//    step s once its left neighbour warp has finished step s-1 and the
-//    previous plane has finished global time t+1 (its values two steps ahead
-//    are loaded early).  These conditions are read from per-warp progress
-//    counters in shared memory (CTA-scope acquire/release), so no CTA-wide
-//    barrier is taken per step and a slow warp only delays the warps that
-//    really depend on it.
-//  * One extra warp talks to the other CTAs: it publishes the progress of
-//    the CTA's last plane with GPU-scope release stores and polls the
-//    previous CTA's progress (relaxed loads, one acquire fence per new
-//    value), forwarding it into shared memory.  Compute warps never execute
-//    a GPU-scope fence.
+//    step s once its left neighbour warp has finished step s-1 and the three
+//    warps of the previous plane whose columns it reads (w-1, w, w+1) have
+//    finished global time t+1 (values two steps ahead are loaded early).
+//    These conditions are read from per-warp progress counters in shared
+//    memory (CTA-scope acquire/release), so no CTA-wide barrier is taken per
+//    step and a warp waits only for the warps it really depends on -- not
+//    for the slowest warp of the previous plane.
+//  * One extra warp talks to the other CTAs: lane w publishes the progress
+//    of warp w of the CTA's last plane with a GPU-scope release store and
+//    polls warp w of the previous CTA (relaxed loads, one acquire fence per
+//    batch of new values), forwarding it into shared memory.  Compute warps
+//    never execute a GPU-scope fence.
+//  * At most one CTA runs per SM (the launch reserves more than half of the
+//    SM's shared memory) and the grid is capped at the SM count: CTAs take
+//    plane groups by ticket, so no plane shares its SM's FP64 pipe with a
+//    plane that is still waiting for its turn.
 // Inside a warp the step body is the software pipeline of k_sweep2.cu:
 // finish point k from a partial sum prepared one step earlier plus the own
 // column (register) and neighbour column (shared ring) terms of the previous
 // step; pre-sum point k+1 from operands loaded one step earlier; load the
 // operands of point k+2.  Every wait is bounded.
+#include <algorithm>
 #include <climits>
 
 #include "smg_internal.cuh"
@@ -80,9 +86,11 @@ struct Sweep3Params {
 };
 
 constexpr int kMaxWarpsPerPlane = 16;  // ny <= 512
-constexpr int kMaxThreads = 544;       // 17 warps: keeps 120 registers per thread
+constexpr int kMaxThreads = 576;       // 16 compute + 2 communication warps
 constexpr int kPrefetch = 10;
 constexpr int kDone = INT_MAX / 2;
+constexpr size_t kOneCtaPerSmSmem = 120 * 1024;
+constexpr unsigned kPublishGapNs = 300;
 // Shared ring of the last kRing values of every column.  A column's value
 // at point k is overwritten by point k + kRing, so a warp may run at most
 // kRing - SB - 2 steps ahead of its right-hand neighbour, which still has
@@ -97,21 +105,22 @@ __device__ __forceinline__ int ld_acq_cta(const int* p) {
 __device__ __forceinline__ void st_rel_cta(int* p, int v) {
   asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
 }
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 template <int W>
 struct Shared3 {
   int wdone[W][kMaxWarpsPerPlane];  // per compute warp: all local steps < value are finished
-  int avail;                        // previous CTA's last plane: global time up to which it is finished
+  int avail[kMaxWarpsPerPlane];     // previous CTA's last plane, per warp: global time finished
   int abort;
   int group;
 };
 
 // FP64 sweeps that use every stencil entry hold twice the operands of the
-// others; they get 9 warps (ny <= 256) and the registers that leaves.
+// others; they get 10 warps (ny <= 256) and the registers that leaves.
 template <int PK, int KIND>
 __host__ __device__ constexpr int max_threads() {
-  return (PK == K64 && KIND == SW_GS_FULL) ? 288 : kMaxThreads;
+  return (PK == K64 && KIND == SW_GS_FULL) ? 320 : kMaxThreads;
 }
 
 template <int PK, int NS, int KIND, int DIR, int W>
@@ -126,8 +135,7 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
   const Grid g = P.g;
   const int NW = (g.ny + 31) >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ncompute = W * NW;
-  const bool comm = warp == ncompute;
+  const int ncompute = W * NW;  // warps ncompute and ncompute + 1 talk to the other CTAs
   constexpr int LEAD = kRing - SB - 2;  // largest lead over the right-hand warp
   // shared value ring: hist[plane][k % kRing][column]
   V* hist = (V*)dyn_smem;
@@ -138,7 +146,6 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
     if (threadIdx.x == 0) {
       sh.group = atomicAdd(&P.ws->ticket, 1);
       sh.abort = 0;
-      sh.avail = 0;
     }
     __syncthreads();
     const int I = sh.group;
@@ -149,48 +156,70 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
       // a warp has trivially finished every step before its first one
       sh.wdone[p][w] = (p < nplanes && w < NW) ? SB * 32 * w - 2 : kDone;
     }
-    if (threadIdx.x == 0 && I == 0) sh.avail = kDone;
+    // nothing precedes the first plane; 0 is below every time a later plane asks for
+    if (threadIdx.x < kMaxWarpsPerPlane) sh.avail[threadIdx.x] = (I == 0) ? kDone : 0;
     __syncthreads();
 
-    if (comm) {
-      // ---- communication warp: publish the last plane, poll the previous CTA
-      if (lane == 0) {
-        const int plast = nplanes - 1;
-        const int gt0 = SA * (I * W + plast);
-        int published = INT_MIN, seen = (I == 0) ? kDone : 0;
-        unsigned long long t_wait = 0;
-        for (;;) {
-          int T = kDone;
-          for (int w = 0; w < NW; ++w) T = min(T, ld_acq_cta(&sh.wdone[plast][w]));
-          if (T != published) {
-            st_release(&P.ws->prog[I], T >= kDone ? kDone : gt0 + T);
-            published = T;
+    if (warp == ncompute) {
+      // ---- publisher warp: lane w publishes the progress of warp w of the
+      // CTA's last plane with a GPU-scope release store whenever it grows
+      const int plast = nplanes - 1;
+      const int gt0 = SA * (I * W + plast);
+      const bool mine = lane < NW;
+      int* out_slot = P.ws->prog + (size_t)I * NW + lane;
+      int published = INT_MIN;
+      for (;;) {
+        const int T = mine ? ld_acq_cta(&sh.wdone[plast][lane]) : kDone;
+        if (__any_sync(0xffffffffu, mine && T != published)) {
+          // one release (one GPU-scope fence) covers every lane's value; a
+          // fence also stalls the SM's other memory traffic, so they are
+          // spaced by a fraction of a step
+          if (mine) st_release(out_slot, T >= kDone ? kDone : gt0 + T);
+          published = T;
+          if (__all_sync(0xffffffffu, T >= kDone)) break;
+          __nanosleep(kPublishGapNs);
+        } else {
+          __nanosleep(32);
+        }
+        if (__any_sync(0xffffffffu, ld_acq_cta(&sh.abort) != 0)) {
+          // release everything downstream; the error word is already set
+          if (mine) st_release(out_slot, kDone);
+          break;
+        }
+      }
+    } else if (warp == ncompute + 1) {
+      // ---- poller warp: lane w forwards the progress of warp w of the
+      // previous CTA's last plane into shared memory (relaxed polls, one
+      // GPU-scope acquire fence per batch of new values)
+      const bool mine = lane < NW;
+      const int* in_slot = P.ws->prog + (size_t)(I - 1) * NW + lane;
+      int seen = (I == 0 || !mine) ? kDone : 0;
+      unsigned long long t_wait = 0;
+      unsigned iter = 0;
+      while (__any_sync(0xffffffffu, seen < kDone)) {
+        const int v = seen < kDone ? ld_relaxed(in_slot) : seen;
+        const bool fresh = v > seen;
+        bool stop = false;
+        if (__any_sync(0xffffffffu, fresh)) {
+          fence_acq_rel_gpu();
+          if (fresh) {
+            seen = v;
+            st_rel_cta(&sh.avail[lane], v);
           }
-          if (T >= kDone) break;
-          if (I > 0 && seen < kDone) {
-            const int v = ld_relaxed(&P.ws->prog[I - 1]);
-            if (v > seen) {
-              __threadfence();
-              seen = v;
-              st_rel_cta(&sh.avail, v);
-              t_wait = 0;
-            } else {
-              // bounded: the previous CTA must make progress within the budget
-              const unsigned long long now = globaltimer_ns();
-              if (t_wait == 0) t_wait = now;
-              else if (now - t_wait > P.budget_ns) {
-                atomicCAS(P.err, 0, DEV_ERR_TIMEOUT);
-                st_rel_cta(&sh.abort, 1);
-                st_release(&P.ws->prog[I], kDone);
-                break;
-              }
-            }
+          t_wait = 0;
+        } else if (lane == 0) {
+          // bounded: the previous CTA must make progress within the budget
+          const unsigned long long now = globaltimer_ns();
+          if (t_wait == 0) t_wait = now;
+          else if (now - t_wait > P.budget_ns) {
+            atomicCAS(P.err, 0, DEV_ERR_TIMEOUT);
+            stop = true;
           }
-          if (ld_relaxed(P.err) != 0) {
-            st_rel_cta(&sh.abort, 1);
-            st_release(&P.ws->prog[I], kDone);
-            break;
-          }
+        }
+        if ((++iter & 63u) == 0 && lane == 0) stop = stop || ld_relaxed(P.err) != 0 || ld_acq_cta(&sh.abort) != 0;
+        if (__shfl_sync(0xffffffffu, stop, 0)) {
+          if (lane == 0) st_rel_cta(&sh.abort, 1);
+          break;
         }
       }
     } else if (warp < W * NW) {
@@ -245,16 +274,15 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
                 ok = have_right >= s - LEAD;
               }
               if (ok) {
-                if (p == 0) {
-                  if (have_up < gt0 + s + 2) {
-                    have_up = ld_acq_cta(&sh.avail);
-                    ok = have_up >= gt0 + s + 2;
-                  }
-                } else if (have_up < s + SA + 2) {
+                // the previous plane's points this warp reads (loads run two
+                // steps ahead) lie in columns 32w-1 .. 32w+32: warps w-1..w+1
+                const int need = (p == 0) ? gt0 + s + 2 : s + SA + 2;
+                if (have_up < need) {
+                  const int* src = (p == 0) ? sh.avail : sh.wdone[p - 1];
                   int T = kDone;
-                  for (int ww = 0; ww < NW; ++ww) T = min(T, ld_acq_cta(&sh.wdone[p - 1][ww]));
+                  for (int ww = max(w - 1, 0); ww <= min(w + 1, NW - 1); ++ww) T = min(T, ld_acq_cta(&src[ww]));
                   have_up = T;
-                  ok = have_up >= s + SA + 2;
+                  ok = have_up >= need;
                 }
               }
               if (ok) break;
@@ -384,7 +412,7 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
   }
   __syncthreads();
   if (sh.group) {
-    for (int q = threadIdx.x; q < ngroups; q += blockDim.x) P.ws->prog[q] = 0;
+    for (int q = threadIdx.x; q < ngroups * NW; q += blockDim.x) P.ws->prog[q] = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
       P.ws->ticket = 0;
@@ -407,9 +435,15 @@ template <int PK, int NS, int W>
 cudaError_t launch_kind(int kind, int dir, const Sweep3Params& P, cudaStream_t st) {
   using V = typename Prec<PK>::vec;
   const int NW = (P.g.ny + 31) / 32;
-  const int nthr = (W * NW + 1) * 32;
-  const size_t smem = sizeof(V) * kRing * (size_t)(NW * 32) * W;  // <= 64 KB for ny <= 512
-  const int grid = (P.g.nx + W - 1) / W;
+  const int nthr = (W * NW + 2) * 32;
+  // the value ring needs <= 64 KB (ny <= 512); reserving more than half of
+  // the SM's 228 KB keeps a second CTA off the SM
+  const size_t smem = std::max(sizeof(V) * kRing * (size_t)(NW * 32) * W, kOneCtaPerSmSmem);
+  int dev = 0, nsm = 0;
+  cudaError_t ae = cudaGetDevice(&dev);
+  if (ae == cudaSuccess) ae = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (ae != cudaSuccess) return ae;
+  const int grid = std::min((P.g.nx + W - 1) / W, nsm);
   auto go = [&](auto kern) {
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -439,9 +473,11 @@ cudaError_t launch_sweep3(const LevelView& L, int kind, int dir, const void* M, 
   if (!((ns == 27 && canonical<27>(L.s)) || (ns == 7 && canonical<7>(L.s)) || (ns == 19 && canonical<19>(L.s))))
     return cudaErrorNotSupported;
   const int NW = (L.g.ny + 31) / 32;
-  const int W = (L.pk != K64 && (2 * NW + 1) * 32 <= kMaxThreads) ? 2 : 1;
+  // two planes per CTA only off FP64: an FP64 plane already keeps its SM's
+  // FP64 pipe busy enough that a second one slows both (measured)
+  const int W = (L.pk != K64 && (2 * NW + 2) * 32 <= kMaxThreads) ? 2 : 1;
   const int maxt = (L.pk == K64 && kind == SW_GS_FULL) ? max_threads<K64, SW_GS_FULL>() : kMaxThreads;
-  if (NW > kMaxWarpsPerPlane || (W * NW + 1) * 32 > maxt) return cudaErrorNotSupported;
+  if (NW > kMaxWarpsPerPlane || (W * NW + 2) * 32 > maxt) return cudaErrorNotSupported;
   Sweep3Params P;
   P.g = L.g;
   P.budget_ns = cfg.budget_ns;

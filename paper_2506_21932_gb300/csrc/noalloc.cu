@@ -18,16 +18,17 @@
 
 namespace {
 
-// Largest x-extent the scratch covers: one progress counter per x-plane.
+// Largest x-extent the scratch covers: progress counters for up to 16 warps
+// of every x-plane.
 constexpr int kNoAllocMaxPlanes = 4096;
 
 struct NoAllocScratch {
-  SweepWs ws;  // ticket, finished-CTA count, prog[kNoAllocMaxPlanes]
+  SweepWs ws;  // ticket, finished-CTA count, prog[kNoAllocMaxPlanes * 16]
   int err[4];  // err[0]: device error word of the bounded waits
 };
-static_assert(sizeof(SweepWs) == 16 + 4 * kNoAllocMaxPlanes, "scratch layout");
+static_assert(sizeof(SweepWs) == 16 + 4 * 16 * kNoAllocMaxPlanes, "scratch layout");
 
-// The scratch itself: about 16 KB, zero at module load, shared by every call
+// The scratch itself: about 256 KB, zero at module load, shared by every call
 // on a device.  In host code this name is only a stand-in for the symbol;
 // kernels get its device address from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
@@ -124,7 +125,7 @@ extern "C" int smg_sweep_noalloc(int op, const int dims[3], int nstencil, const 
   cfg.budget_ns = (unsigned long long)spin_budget_ms * 1000000ull;
   // the progress counters, ticket and error word must start at zero; clear
   // them (and nothing else) for this call
-  SMG_CUDA_TRY(cudaMemsetAsync(S, 0, 16 + 4 * (size_t)dims[0], st));
+  SMG_CUDA_TRY(cudaMemsetAsync(S, 0, 16 + 4 * 16 * (size_t)dims[0], st));
   SMG_CUDA_TRY(cudaMemsetAsync(S->err, 0, sizeof(S->err), st));
   SMG_CUDA_TRY(launch_sweep(L, kind, dir, M, nullptr, nullptr, dinv, relax_w, b, u, &S->ws, S->err, cfg, st));
   int herr = 0;

@@ -47,11 +47,14 @@ struct Stencil {
 
 // Per-sweep device workspace for the wavefront kernels: progress of every
 // plane, a ticket that hands out planes in order, a count of finished CTAs.
+// Progress slots: one per x-plane (plane-per-CTA kernels) or one per x-plane
+// group and 32-column warp (warp-pipelined kernel): 4096 planes x 16 warps.
+constexpr int kProgSlots = 4096 * 16;
 struct SweepWs {
   int ticket;
   int finished;
   int pad[2];
-  int prog[4096];  // prog[i] = global time step up to which plane i is done
+  int prog[kProgSlots];  // global time step up to which a plane (or a plane's warp) is done
 };
 
 // Kernel-visible error word values (mirror smg_status).
