@@ -50,8 +50,14 @@ WORKLOADS = {
                transfer=1, precision=0, krylov=2, tol=1e-8, block=3),
     "c4_fp32": dict(desc="block3x3_7pt_128x128x64_bsgs_pc8c_fgmres30_fp32hier", dims=(128, 128, 64), gen="blk",
                     smoother=0, transfer=1, precision=1, krylov=2, tol=1e-8, block=3),
-    "c5": dict(desc="varcoef7_256^3_sgs_fw27v_pcg_fp64", dims=(256, 256, 256), gen="fv", smoother=0, transfer=0,
-               precision=0, krylov=0, tol=1e-9),
+    # learned post-smoother: trained on 64^3 fields (2000 pairs), evaluated on
+    # an unseen field at 256^3 with FPCG; the plain GS V-cycle PCG solve of the
+    # same problem is timed beside it
+    "c5": dict(desc="varcoef7_256^3_sgs_fw27v_fpcg_cnn_fp64", dims=(256, 256, 256), gen="fv", smoother=0,
+               transfer=0, precision=0, krylov=1, tol=1e-9, learned=dict(dims=(64, 64, 64), fields=20, pairs=2000,
+                                                                          batch=4, lr=1e-3)),
+    "c5_plain": dict(desc="varcoef7_256^3_sgs_fw27v_pcg_fp64", dims=(256, 256, 256), gen="fv", smoother=0,
+                     transfer=0, precision=0, krylov=0, tol=1e-9),
 }
 DEFAULT = "c2"
 HBM_PEAK_FALLBACK = 6800.0
@@ -62,21 +68,54 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def make_problem(w, seed, device):
+def make_problem(w, seed, device, with_logk=False):
     from paper_2506_21932_gb300 import inputs as I
     d = w["dims"]
     n = d[0] * d[1] * d[2]
     B = w.get("block", 1)
+    logk = None
     if w["gen"] == "lap":
         off, A = I.OFF7, I.laplace7(d, device=device)
     elif w["gen"] == "q1":
         off, A = I.OFF27, I.q1_aniso27(d, seed, device=device)
     elif w["gen"] == "fv":
-        off, A = I.OFF7, I.varcoef7(d, seed, device=device)[0]
+        off, (A, logk) = I.OFF7, I.varcoef7(d, seed, device=device)
     else:
         off, A = I.OFF7, I.block7_layered(d, seed, device=device)
     b = I.rhs(n * B, 1000 + seed, device=device)
+    if with_logk:
+        return off, A.contiguous(), b.contiguous(), (None if logk is None else logk.contiguous())
     return off, A.contiguous(), b.contiguous()
+
+
+def train_post_smoother(w, dev):
+    """Trains the learned post-smoother on seeded 64^3 fields (training seeds
+    1000 + f) with the library's own kernels; returns (theta, info)."""
+    import torch
+    from paper_2506_21932_gb300 import smg
+    from paper_2506_21932_gb300.learned import PostSmootherTrainer
+    cfg = w["learned"]
+    tw = dict(w, dims=cfg["dims"])
+    mgs, lks = [], []
+    for f in range(cfg["fields"]):
+        off, A, _, logk = make_problem(tw, 1000 + f, dev, with_logk=True)
+        mgs.append(smg.SMG(cfg["dims"], off, A, smoother=w["smoother"], transfer=w["transfer"], krylov=1))
+        lks.append(logk)
+    tr = PostSmootherTrainer(mgs, lks, seed=0, lr=cfg["lr"], batch=cfg["batch"])
+    loss0 = tr.eval_loss(8)
+    steps = cfg["pairs"] // cfg["batch"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = tr.train(steps)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    loss1 = tr.eval_loss(8)
+    theta = tr.theta.clone()
+    for m in mgs:
+        m.close()
+    return theta, {"train_s": round(train_s, 3), "pairs": steps * cfg["batch"], "fields": cfg["fields"],
+                   "grid": list(cfg["dims"]), "loss_before": round(loss0, 6), "loss_after": round(loss1, 6),
+                   "loss_last_steps": round(sum(losses[-20:]) / min(20, len(losses)), 6)}
 
 
 def measured_peaks():
@@ -144,15 +183,24 @@ def run_ours(args, w, rank, world):
     torch.cuda.set_device(dev)
     smg.lib()
     B = w.get("block", 1)
-    off, A, b = make_problem(w, rank, dev)
+    off, A, b, logk = make_problem(w, rank, dev, with_logk=True)
     n = b.numel()
     x = torch.zeros_like(b)
     st = torch.cuda.current_stream()
     kw = dict(block=B, smoother=w["smoother"], transfer=w["transfer"], precision=w["precision"],
               krylov=w["krylov"], restart=30)
+    theta, learned_info = (None, None)
+    if w.get("learned"):
+        theta, learned_info = train_post_smoother(w, dev)
+
+    def make_ctx(Amat, lk=logk):
+        h = smg.SMG(w["dims"], off, Amat, **kw)
+        if theta is not None:
+            h.set_learned_smoother(theta, lk)
+        return h
 
     def step():
-        h = smg.SMG(w["dims"], off, A, **kw)
+        h = make_ctx(A)
         x.zero_()
         it, rr, rc = h.solve(b, x, tol=w["tol"], maxit=1000, check=False)
         s = h.stats()
@@ -188,7 +236,24 @@ def run_ours(args, w, rank, world):
     s = results[-1][3]
     clocks = clk.summary()
 
-    # --- V-cycle throughput on a persistent hierarchy -------------------------
+    # --- the same problem with the plain V-cycle and PCG, for comparison ------
+    plain = None
+    if theta is not None:
+        hp = smg.SMG(w["dims"], off, A, **dict(kw, krylov=0))
+        hp.close()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        hp = smg.SMG(w["dims"], off, A, **dict(kw, krylov=0))
+        x.zero_()
+        pit, prr, prc = hp.solve(b, x, tol=w["tol"], maxit=1000, check=False)
+        hp.close()
+        e1.record(st)
+        torch.cuda.synchronize()
+        plain = {"krylov": "PCG", "smoother": "plain GS V-cycle", "ms": round(e0.elapsed_time(e1), 3),
+                 "iterations": pit, "final_true_relres": prr, "status": prc}
+
+    # --- V-cycle throughput on a persistent hierarchy (plain V-cycle) ----------
     h = smg.SMG(w["dims"], off, A, **kw)
     z = torch.empty_like(b)
     for _ in range(2):
@@ -255,9 +320,12 @@ def run_ours(args, w, rank, world):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic_bytes_per_point": bytes_pt, "launch_ms": round(k_ms, 4)}
 
+    extra = {}
+    if learned_info is not None:
+        extra = {"learned": learned_info, "plain_pcg": plain}
     if args.no_e2e:
         return dict(ms=ms, iters=iters, relres=relres, stats=s, clocks=clocks, launches=launches, vc_ms=vc_ms,
-                    vc_gbs=vc_gbs, hbm=hbm, roof=roof, e2e_ms=float("nan"), h2d=0, d2h=0)
+                    vc_gbs=vc_gbs, hbm=hbm, roof=roof, e2e_ms=float("nan"), h2d=0, d2h=0, extra=extra)
 
     # --- e2e: host buffers, copies inside the timed region ---------------------
     A_h = A.cpu().pin_memory()
@@ -266,11 +334,15 @@ def run_ours(args, w, rank, world):
     A_d = torch.empty_like(A)
     b_d = torch.empty_like(b)
     x_d = torch.empty_like(b)
+    lk_h = None if logk is None else logk.cpu().pin_memory()
+    lk_d = None if logk is None else torch.empty_like(logk)
 
     def e2e_step():
         A_d.copy_(A_h, non_blocking=True)
         b_d.copy_(b_h, non_blocking=True)
-        hh = smg.SMG(w["dims"], off, A_d, **kw)
+        if lk_d is not None:
+            lk_d.copy_(lk_h, non_blocking=True)
+        hh = make_ctx(A_d, lk_d)
         x_d.zero_()
         hh.solve(b_d, x_d, tol=w["tol"], maxit=1000, check=False)
         hh.close()
@@ -290,7 +362,7 @@ def run_ours(args, w, rank, world):
 
     return dict(ms=ms, iters=iters, relres=relres, stats=s, clocks=clocks, launches=launches, vc_ms=vc_ms,
                 vc_gbs=vc_gbs, hbm=hbm, roof=roof, e2e_ms=max(e2e_ms, e2e_wall),
-                h2d=A.numel() * 8 + n * 8, d2h=n * 8)
+                h2d=A.numel() * 8 + n * 8 + (0 if logk is None else logk.numel() * 8), d2h=n * 8, extra=extra)
 
 
 def oracle_sample(w, seed=0):
@@ -373,6 +445,8 @@ def main():
         cpu = {"value": round(o["value"], 3), "unit": "s", "cores": 1, "kind": "oracle",
                "sample": "grid %s (1/%d of the unknowns), full set-up + solve in %d iterations, time x%d" % (
                    "x".join(map(str, o["grid"])), o["scale"], o["iters"], o["scale"])}
+        if w.get("learned"):
+            cpu["sample"] += "; plain V-cycle (the timed oracle runs no network)"
     s = r["stats"]
     line = {"metric": metric, "value": round(r["ms"] / 1e3, 5), "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(r["ms"], 3), "higher_is_better": False, "scaling": "weak",
@@ -388,6 +462,7 @@ def main():
             "e2e": {"value": round(r["e2e_ms"] / 1e3, 5), "unit": "s", "h2d_bytes_per_step": int(r["h2d"]),
                     "d2h_bytes_per_step": int(r["d2h"])},
             "gpu_launches": int(r["launches"]), "clocks": r["clocks"]}
+    line.update(r.get("extra", {}))
     print(json.dumps(line), flush=True)
 
 

@@ -212,14 +212,60 @@ int smg_derive_chains(int dim, int nr, const int* roff, int na, const int* aoff,
                       int max_chains, int* chains);
 
 /* ---------------------------------------------------------------------------
+ * Learned post-smoother (not in the paper).  A three-layer 3x3x3
+ * convolutional network f (2 -> 16 -> 16 -> 1 channels, ReLU after the first
+ * two layers, zero padding) maps the scaled residual and the log-coefficient
+ * field to a correction.  Convolutions are implicit GEMMs on the tensor cores
+ * with BF16 operands and FP32 accumulation.
+ * Parameters: an FP32 device vector of smg_cnn_param_count() = 8241 values,
+ * W1[16][2][3][3][3] b1[16] W2[16][16][3][3][3] b2[16] W3[1][16][3][3][3]
+ * b3[1]; tap (a,b,c) multiplies the input at offset (a-1, b-1, c-1).
+ * Volumes: FP32, grid layout of the matrices; in2 = two planes [2][n]
+ * (channel 0, channel 1).  ws: caller-allocated device workspace of at least
+ * smg_cnn_workspace_bytes(dims) bytes.  All calls are asynchronous on the
+ * stream except smg_cnn_forward (synchronises).  Errors: SMG_EINVAL for bad
+ * sizes, NULL pointers or a short workspace; SMG_ECUDA.
+ * ------------------------------------------------------------------------- */
+int smg_cnn_param_count(void);
+int smg_cnn_workspace_bytes(const int dims[3], size_t* bytes);
+/* out[n] = f(in2) */
+int smg_cnn_forward(const int dims[3], const float* theta, const float* in2, float* out, void* ws, size_t ws_bytes,
+                    void* stream);
+/* loss += mean_p (f(in2)_p - target_p)^2 ; grad[8241] += d loss / d theta
+ * (loss is one FP32 device scalar; both are accumulated, not overwritten). */
+int smg_cnn_loss_grad(const int dims[3], const float* theta, const float* in2, const float* target, float* grad,
+                      float* loss, void* ws, size_t ws_bytes, void* stream);
+/* One Adam step (bias-corrected, step counts from 1) on n parameters with the
+ * gradient multiplied by grad_scale. */
+int smg_cnn_adam(int n, float* theta, float* m, float* v, const float* grad, int step, float lr, float beta1,
+                 float beta2, float eps, float grad_scale, void* stream);
+/* Attaches the network as a post-smoother of the finest level, applied after
+ * every V-cycle: r' = r - A z, s = ||r'||_2 / sqrt(n),
+ * delta = s * f(r'/s, logk), and z += delta only if ||r' - A delta||_2 <
+ * ||r'||_2 (otherwise the plain V-cycle result is kept).  theta (FP32
+ * [8241]) is packed at this call; logk (double [n], the log of the diffusion
+ * coefficient) must stay valid while attached.  theta == NULL detaches.
+ * The preconditioner is then nonlinear: the context's Krylov method must be
+ * FPCG or FGMRES (SMG_EINVAL otherwise); one unknown per point only. */
+int smg_set_learned_smoother(smg_t h, const float* theta, const double* logk, void* stream);
+/* One training pair for the post-smoother, built on the device from a known
+ * error e0 (double [n], device): r0 = A e0, z = V-cycle(r0) (the plain one,
+ * even when a network is attached), e1 = e0 - z (the exact error the V-cycle
+ * leaves), r' = A e1, s = ||r'||_2 / sqrt(n); writes in2 = [r'/s ; logk]
+ * (float [2][n]) and target = e1 / s (float [n]).  Synchronous on the
+ * stream.  Errors: SMG_EINVAL (NULL pointer, B != 1), SMG_ECUDA, sweep
+ * errors. */
+int smg_learned_sample(smg_t h, const double* e0, const double* logk, float* in2, float* target, void* stream);
+
+/* ---------------------------------------------------------------------------
  * One Gauss-Seidel or ILU(0) triangular sweep that allocates no memory.
  * No counterpart in the paper: it exists for callers that cannot let a
  * library allocate device memory -- applications that own every byte of the
  * GPU through their own pool, fixed-budget real-time or embedded callers,
  * plug-ins whose host forbids cudaMalloc (it synchronises the device and
  * fragments the host's pool).  It needs no context: the caller passes the
- * matrix and vectors, and the sweep's scratch (per-plane progress counters,
- * plane ticket, error word: about 16 KB) is a fixed array in device memory
+ * matrix and vectors, and the sweep's scratch (progress counters per plane
+ * and warp, plane ticket, error word: about 256 KB) is a fixed array in device memory
  * that every GPU which loads this library keeps until the process exits.
  *  op        SMG_OP_GS_FORWARD / SMG_OP_GS_BACKWARD / SMG_OP_GS_ZERO (u is
  *            the iterate, updated in place, b the right-hand side, dinv the
@@ -227,7 +273,7 @@ int smg_derive_chains(int dim, int nr, const int* roff, int na, const int* aoff,
  *            ILU(0) factors of smg_level_copy which 1, dinv unused, u may
  *            equal b), SMG_OP_ILU_UPPER (u = U^{-1} b, dinv = 1/u_pp, u may
  *            equal b).  The results equal smg_level_apply's for the same op.
- *  dims      host int[3]; nx <= 4096 (the scratch holds one counter per
+ *  dims      host int[3]; nx <= 4096 (the scratch holds 16 counters per
  *            x-plane), ny <= 1024, nz <= 4096.
  *  nstencil, offsets  host; offsets in lexicographic order (dx slowest),
  *            unique, symmetric, with the centre (no reordered copy is made).

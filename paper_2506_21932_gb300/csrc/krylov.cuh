@@ -5,6 +5,7 @@
 // Slots of the device scalar array used by the Krylov loops.
 enum {
   SC_RHO = 0, SC_PQ = 1, SC_RR = 2, SC_RZ = 3, SC_ALPHA = 4, SC_BETA = 5, SC_BB = 6, SC_WW = 7,
+  SC_LS_RR = 8, SC_LS_INVS = 9, SC_LS_S = 10, SC_LS_WW = 11,  // learned post-smoother
   SC_H = 16,  // GMRES: Gram-Schmidt coefficients h[0..64)
   SC_H2 = 96, // GMRES: second Gram-Schmidt pass
   SC_COUNT = 192

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "chains.h"
+#include "cnn.cuh"
 #include "krylov.cuh"
 #include "smg_internal.cuh"
 
@@ -94,6 +95,11 @@ struct smg_ctx {
   cudaStream_t cap = nullptr;  // library-owned stream for graph capture / replay
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int kernels_per_vcycle = 0;
+  // learned post-smoother of the finest level (null when detached)
+  const double* ls_logk = nullptr;
+  void* ls_ws = nullptr;
+  CnnWork ls_w{};
+  double *ls_r = nullptr, *ls_d = nullptr, *ls_t = nullptr;
 };
 
 static int dev_alloc(smg_ctx* h, void** p, size_t bytes) {
@@ -237,6 +243,27 @@ static int coarse_solve(smg_ctx* h, const void* f, void* u, cudaStream_t st) {
   return SMG_OK;
 }
 
+// Learned post-smoother on the finest level (not in the paper), applied to
+// the V-cycle's result z: r' = r - A z, s = rms(r'), delta = s f(r'/s, logk),
+// z += delta only if ||r' - A delta|| < ||r'||.  The decision is taken on the
+// device from the two norms; nothing is read back.
+static int learned_post_smooth(smg_ctx* h, const double* r, double* z, cudaStream_t st) {
+  const Level& L0 = h->L[0];
+  const long long n = L0.g.n;
+  const LevelView A0 = view(h, L0, false);
+  CnnDims d{L0.g.nx, L0.g.ny, L0.g.nz};
+  SMG_CUDA_TRY(launch_spmv(A0, z, r, h->ls_r, 1, st));
+  SMG_CUDA_TRY(kry_dot(n, h->ls_r, h->ls_r, h->sc, SC_LS_RR, h->rw, st));
+  SMG_CUDA_TRY(cnn_post_glue(0, n, nullptr, nullptr, nullptr, h->sc + SC_LS_RR, nullptr, h->sc + SC_LS_INVS, st));
+  SMG_CUDA_TRY(cnn_pack_input(n, h->ls_r, h->ls_logk, h->sc + SC_LS_INVS, 0.0, h->ls_w.a0, st));
+  SMG_CUDA_TRY(cnn_forward_packed(d, h->ls_w, st));
+  SMG_CUDA_TRY(cnn_post_glue(1, n, h->ls_w.y, nullptr, h->ls_d, h->sc + SC_LS_S, nullptr, nullptr, st));
+  SMG_CUDA_TRY(launch_spmv(A0, h->ls_d, h->ls_r, h->ls_t, 1, st));
+  SMG_CUDA_TRY(kry_dot(n, h->ls_t, h->ls_t, h->sc, SC_LS_WW, h->rw, st));
+  SMG_CUDA_TRY(cnn_post_glue(2, n, nullptr, z, h->ls_d, h->sc + SC_LS_WW, h->sc + SC_LS_RR, nullptr, st));
+  return SMG_OK;
+}
+
 // z = M^{-1} r, one V(1,1)-cycle (Sec. 2): pre-smooth from zero, residual,
 // restrict; direct solve on the coarsest level; prolong, correct, post-smooth.
 static int vcycle_body(smg_ctx* h, const double* r, double* z, cudaStream_t st) {
@@ -268,6 +295,7 @@ static int vcycle_body(smg_ctx* h, const double* r, double* z, cudaStream_t st) 
     TRY(smooth_post(h, L, F(l), U(l), st));
   }
   if (h->pk != K64) SMG_CUDA_TRY(launch_cast_f2d((const float*)u0, z, n0, st));
+  if (h->ls_logk) TRY(learned_post_smooth(h, r, z, st));
   return SMG_OK;
 }
 
@@ -914,6 +942,65 @@ extern "C" int smg_level_apply(smg_t h, int l, int op, const void* x, const void
       return SMG_EINVAL;
   }
   return fetch_err(h, st);
+}
+
+static int ensure_ls_buffers(smg_ctx* h) {
+  if (h->ls_ws) return SMG_OK;
+  const Level& L0 = h->L[0];
+  const long long n = L0.g.n;
+  CnnDims d{L0.g.nx, L0.g.ny, L0.g.nz};
+  TRY(dev_alloc(h, &h->ls_ws, cnn_workspace_bytes(d)));
+  TRY(dalloc(h, &h->ls_r, n));
+  TRY(dalloc(h, &h->ls_d, n));
+  TRY(dalloc(h, &h->ls_t, n));
+  cnn_carve(d, h->ls_ws, h->ls_w);
+  return SMG_OK;
+}
+
+extern "C" int smg_learned_sample(smg_t h, const double* e0, const double* logk, float* in2, float* target,
+                                  void* stream) {
+  if (!h || !e0 || !logk || !in2 || !target || h->B != 1) return SMG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  TRY(ensure_ls_buffers(h));
+  const Level& L0 = h->L[0];
+  const long long n = L0.g.n;
+  const LevelView A0 = view(h, L0, false);
+  SMG_CUDA_TRY(launch_spmv(A0, e0, e0, h->ls_r, 0, st));  // r0 = A e0
+  const double* saved = h->ls_logk;
+  h->ls_logk = nullptr;  // the plain V-cycle
+  const int rc = vcycle_body(h, h->ls_r, h->ls_d, st);
+  h->ls_logk = saved;
+  TRY(rc);
+  SMG_CUDA_TRY(cnn_sample_glue(0, n, e0, h->ls_d, h->ls_t, nullptr, nullptr, nullptr, nullptr, nullptr, st));
+  SMG_CUDA_TRY(launch_spmv(A0, h->ls_t, h->ls_t, h->ls_r, 0, st));  // r' = A e1
+  SMG_CUDA_TRY(kry_dot(n, h->ls_r, h->ls_r, h->sc, SC_LS_RR, h->rw, st));
+  SMG_CUDA_TRY(cnn_post_glue(0, n, nullptr, nullptr, nullptr, h->sc + SC_LS_RR, nullptr, h->sc + SC_LS_INVS, st));
+  SMG_CUDA_TRY(cnn_sample_glue(1, n, nullptr, nullptr, h->ls_t, h->ls_r, logk, h->sc + SC_LS_INVS, in2, target, st));
+  return fetch_err(h, st);
+}
+
+extern "C" int smg_set_learned_smoother(smg_t h, const float* theta, const double* logk, void* stream) {
+  if (!h) return SMG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!theta) {
+    h->ls_logk = nullptr;
+    if (h->vgraph) {
+      cudaGraphExecDestroy(h->vgraph);
+      h->vgraph = nullptr;
+    }
+    return SMG_OK;
+  }
+  if (!logk || h->B != 1 || h->opt.krylov == SMG_KRYLOV_PCG) return SMG_EINVAL;
+  TRY(ensure_ls_buffers(h));
+  SMG_CUDA_TRY(cnn_pack(theta, h->ls_w.pk, st));
+  h->ls_logk = logk;
+  // a captured V-cycle graph does not contain the post-smoother yet
+  if (h->vgraph) {
+    cudaGraphExecDestroy(h->vgraph);
+    h->vgraph = nullptr;
+  }
+  SMG_CUDA_TRY(cudaStreamSynchronize(st));
+  return SMG_OK;
 }
 
 extern "C" int smg_selftest_wait(smg_t h, int budget_ms, void* stream) {

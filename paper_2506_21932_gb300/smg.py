@@ -69,8 +69,52 @@ def lib():
         L.smg_launch_count.restype = ctypes.c_longlong
         L.smg_selftest_wait.argtypes = [vp, i, vp]
         L.smg_sweep_noalloc.argtypes = [i, ip, i, ip, vp, vp, vp, vp, d, i, vp]
+        sz = ctypes.c_size_t
+        f = ctypes.c_float
+        L.smg_cnn_workspace_bytes.argtypes = [ip, ctypes.POINTER(sz)]
+        L.smg_cnn_forward.argtypes = [ip, vp, vp, vp, vp, sz, vp]
+        L.smg_cnn_loss_grad.argtypes = [ip, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.smg_cnn_adam.argtypes = [i, vp, vp, vp, vp, i, f, f, f, f, f, vp]
+        L.smg_set_learned_smoother.argtypes = [vp, vp, vp, vp]
+        L.smg_learned_sample.argtypes = [vp, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
+
+
+# ---- learned post-smoother network (FP32 tensors on the device) ------------
+
+def cnn_param_count():
+    return int(lib().smg_cnn_param_count())
+
+
+def cnn_workspace(dims):
+    """Allocates (through torch) the device workspace the network needs."""
+    import torch
+    nb = ctypes.c_size_t(0)
+    rc = lib().smg_cnn_workspace_bytes(_iarr(dims), ctypes.byref(nb))
+    if rc != OK:
+        raise SmgError(rc, "smg_cnn_workspace_bytes")
+    return torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+
+
+def cnn_forward(dims, theta, in2, out, ws, stream=None):
+    rc = lib().smg_cnn_forward(_iarr(dims), _ptr(theta), _ptr(in2), _ptr(out), _ptr(ws), ws.numel(), _stream(stream))
+    if rc != OK:
+        raise SmgError(rc, "smg_cnn_forward")
+
+
+def cnn_loss_grad(dims, theta, in2, target, grad, loss, ws, stream=None):
+    rc = lib().smg_cnn_loss_grad(_iarr(dims), _ptr(theta), _ptr(in2), _ptr(target), _ptr(grad), _ptr(loss), _ptr(ws),
+                                 ws.numel(), _stream(stream))
+    if rc != OK:
+        raise SmgError(rc, "smg_cnn_loss_grad")
+
+
+def cnn_adam(theta, m, v, grad, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0, stream=None):
+    rc = lib().smg_cnn_adam(theta.numel(), _ptr(theta), _ptr(m), _ptr(v), _ptr(grad), step, lr, beta1, beta2, eps,
+                            grad_scale, _stream(stream))
+    if rc != OK:
+        raise SmgError(rc, "smg_cnn_adam")
 
 
 def sweep_noalloc(op, dims, offsets, M, dinv, b, u, relax_w=1.0, spin_budget_ms=0, stream=None):
@@ -207,6 +251,19 @@ class SMG:
         rc = self._lib.smg_level_apply(self.h, l, op, _ptr(x), _ptr(b), _ptr(y), _stream(stream))
         if rc != OK:
             raise SmgError(rc, "smg_level_apply")
+
+    def set_learned_smoother(self, theta, logk, stream=None):
+        """Attach (theta: FP32 [8241], logk: float64 [n]) or detach (None)."""
+        self._ls = (theta, logk)  # keep the tensors alive while attached
+        rc = self._lib.smg_set_learned_smoother(self.h, _ptr(theta), _ptr(logk), _stream(stream))
+        if rc != OK:
+            raise SmgError(rc, "smg_set_learned_smoother")
+
+    def learned_sample(self, e0, logk, in2, target, stream=None):
+        """One training pair from a known error e0 (see smg_learned_sample)."""
+        rc = self._lib.smg_learned_sample(self.h, _ptr(e0), _ptr(logk), _ptr(in2), _ptr(target), _stream(stream))
+        if rc != OK:
+            raise SmgError(rc, "smg_learned_sample")
 
     def selftest_wait(self, budget_ms=20, stream=None):
         """Runs one bounded device wait that must time out; returns the status."""
