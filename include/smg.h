@@ -241,8 +241,9 @@ int smg_cnn_adam(int n, float* theta, float* m, float* v, const float* grad, int
                  float beta2, float eps, float grad_scale, void* stream);
 /* Attaches the network as a post-smoother of the finest level, applied after
  * every V-cycle: r' = r - A z, s = ||r'||_2 / sqrt(n),
- * delta = s * f(r'/s, logk), and z += delta only if ||r' - A delta||_2 <
- * ||r'||_2 (otherwise the plain V-cycle result is kept).  theta (FP32
+ * delta = s * D^-1 f(r'/s, logk) with D the diagonal of A (the network
+ * learns a correction relative to a Jacobi step), and z += delta only if
+ * ||r' - A delta||_2 < ||r'||_2 (otherwise the plain V-cycle result is kept).  theta (FP32
  * [8241]) is packed at this call; logk (double [n], the log of the diffusion
  * coefficient) must stay valid while attached.  theta == NULL detaches.
  * The preconditioner is then nonlinear: the context's Krylov method must be
@@ -252,10 +253,22 @@ int smg_set_learned_smoother(smg_t h, const float* theta, const double* logk, vo
  * error e0 (double [n], device): r0 = A e0, z = V-cycle(r0) (the plain one,
  * even when a network is attached), e1 = e0 - z (the exact error the V-cycle
  * leaves), r' = A e1, s = ||r'||_2 / sqrt(n); writes in2 = [r'/s ; logk]
- * (float [2][n]) and target = e1 / s (float [n]).  Synchronous on the
+ * (float [2][n]) and target = D e1 / s (float [n], D the diagonal of A: the
+ * network output that would reproduce e1 exactly).  Synchronous on the
  * stream.  Errors: SMG_EINVAL (NULL pointer, B != 1), SMG_ECUDA, sweep
  * errors. */
 int smg_learned_sample(smg_t h, const double* e0, const double* logk, float* in2, float* target, void* stream);
+/* Loss and gradient of one training pair on this context's finest grid
+ * (ws: smg_cnn_workspace_bytes of that grid).  kind SMG_LOSS_ERROR: the
+ * error MSE of smg_cnn_loss_grad (target used).  kind SMG_LOSS_RESIDUAL:
+ * the residual the correction leaves, loss += |A D^-1 y - in2[0..n)|^2 / n
+ * with y = f(in2), A the finest matrix (FP64, assumed symmetric) and D its
+ * diagonal (target unused): the quantity the acceptance test compares.
+ * Both accumulate into grad and loss; asynchronous on the stream.
+ * Errors: SMG_EINVAL (NULL pointer, B != 1, bad kind, short ws), SMG_ECUDA. */
+enum { SMG_LOSS_ERROR = 0, SMG_LOSS_RESIDUAL = 1 };
+int smg_learned_loss_grad(smg_t h, const float* theta, const float* in2, const float* target, int kind, float* grad,
+                          float* loss, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * One Gauss-Seidel or ILU(0) triangular sweep that allocates no memory.

@@ -163,10 +163,11 @@ def adam_init(params):
     return (0, z, [(np.zeros_like(W), np.zeros_like(b)) for W, b in params])
 
 
-def post_smooth(apply_A, r, z, logk, params, bf=False):
+def post_smooth(apply_A, r, z, logk, params, bf=False, dinv=None):
     """Learned post-smoother step on the finest level.
 
-    r' = r - A z,  s = ||r'||_2 / sqrt(n),  delta = s * f(r'/s, logk),
+    r' = r - A z,  s = ||r'||_2 / sqrt(n),  delta = s * dinv * f(r'/s, logk)
+    (dinv = 1 / diag(A), the network corrects a Jacobi step; None = 1),
     and z + delta is returned if ||r' - A delta||_2 < ||r'||_2, else z.
     Vectors are flat in grid order (dims from logk's shape, [X, Y, Z]).
     Returns (new z, accepted)."""
@@ -177,23 +178,25 @@ def post_smooth(apply_A, r, z, logk, params, bf=False):
     inv_s = 1.0 / s if s > 0 else 0.0
     x = np.stack([(rp * inv_s).reshape(dims), logk])
     y, _ = forward(params, x, bf)
-    delta = s * y.reshape(-1)
+    delta = s * (1.0 if dinv is None else dinv) * y.reshape(-1)
     t = rp - apply_A(delta)
     if np.dot(t, t) < np.dot(rp, rp):
         return z + delta, True
     return z.copy(), False
 
 
-def training_pair(apply_A, vcycle, e0, logk):
+def training_pair(apply_A, vcycle, e0, logk, diag=None):
     """One training pair from a known error e0: the V-cycle is applied to
     r0 = A e0, e1 = e0 - V(r0) is the error it leaves, r' = A e1 and
     s = ||r'||_2 / sqrt(n).  Returns (input [2, X, Y, Z], target [1, X, Y, Z])
-    = ([r'/s, logk], e1/s)."""
+    = ([r'/s, logk], diag * e1 / s): the network output y for which the
+    post-smoother's correction s * y / diag equals e1 (diag None = 1)."""
     dims = logk.shape
     e1 = e0 - vcycle(apply_A(e0))
     rp = apply_A(e1)
     s = np.sqrt(np.dot(rp, rp) / rp.size)
-    return np.stack([(rp / s).reshape(dims), logk]), (e1 / s).reshape((1,) + dims)
+    t = e1 / s if diag is None else diag * e1 / s
+    return np.stack([(rp / s).reshape(dims), logk]), t.reshape((1,) + dims)
 
 
 def identity_network(gain=1.0):
@@ -207,3 +210,32 @@ def identity_network(gain=1.0):
     W3 = np.zeros((1, 16, 3, 3, 3))
     W3[0, 0, 1, 1, 1], W3[0, 1, 1, 1, 1] = gain, -gain
     return [(W1, np.zeros(16)), (W2, np.zeros(16)), (W3, np.zeros(1))]
+
+
+def residual_loss_and_grads(params, x, apply_A, bf=False, dinv=None):
+    """Loss of the correction measured by the residual it leaves: with
+    rhat = x[0] (the scaled residual r'/s) and y = f(x), the scaled
+    correction is dinv * y and q = A (dinv * y) - rhat, loss = mean(q^2),
+    i.e. the squared residual of the corrected iterate relative to n.  A must
+    be symmetric (apply_A maps a flat vector to a flat vector), so
+    d loss / d y = 2 dinv * (A q) / n.  dinv None = 1.  In bf16 mode y is the
+    FP32 network output, q and A q are FP64 and the back-propagated signal is
+    rounded to BF16 as in mse_loss_and_grads."""
+    y, acts = forward(params, x, bf)
+    cp = _cast_params(params, bf)
+    n = y.size
+    dv = 1.0 if dinv is None else dinv
+    q = apply_A(dv * y.reshape(-1)) - x[0].reshape(-1)
+    loss = float(np.dot(q, q) / n)
+    g = (2.0 * dv * apply_A(q) / n).reshape(y.shape)
+    g = bf16(g) if bf else g
+    grads = [None] * len(params)
+    for l in range(len(params) - 1, -1, -1):
+        W, _ = cp[l]
+        if l < len(params) - 1:
+            g = g * (acts[l + 1] > 0.0)
+            g = bf16(g) if bf else g
+        gx, gW, gb = conv3d_backward(acts[l], W, g)
+        grads[l] = (gW, gb)
+        g = gx
+    return loss, grads

@@ -47,12 +47,21 @@ size_t cnn_workspace_bytes(const CnnDims& d);
 void cnn_carve(const CnnDims& d, void* base, CnnWork& w);
 // y = f(act0) for the packed network (act0 already filled)
 cudaError_t cnn_forward_packed(const CnnDims& d, CnnWork& w, cudaStream_t st);
+// grad += d loss / d theta, from the output gradient in w.g3 (after a forward)
+cudaError_t cnn_backward(const CnnDims& d, CnnWork& w, float* grad, cudaStream_t st);
+int cnn_check_dims(const int dims[3], CnnDims& d);
+// Residual-loss glue: which 0 -> out = a - f[0..n) (FP64); which 1 ->
+// *loss += a[0] / n; which 2 -> g16 channel 0 = bf16(2 dinv a / n), others
+// 0; which 3 -> out = dinv * f.
+cudaError_t cnn_resid_glue(int which, long long n, const double* a, const float* f, const double* dinv, double* out,
+                           float* loss, __nv_bfloat16* g16, cudaStream_t st);
 // Post-smoother glue: which 0 -> out[0..1] = (1/rms, rms) of the sum of
-// squares a[0] over n points; 1 -> delta = a[0] * y; 2 -> z += delta where
-// a[0] < b[0].
+// squares a[0] over n points; 1 -> delta = a[0] * dinv * y; 2 -> z += delta
+// where a[0] < b[0].
 cudaError_t cnn_post_glue(int which, long long n, const float* y, double* z, double* delta, const double* a,
-                          const double* b, double* out, cudaStream_t st);
+                          const double* b, const double* dinv, double* out, cudaStream_t st);
 // Training-pair glue: which 0 -> e1 = e0 - z; which 1 -> in2 = [rp * inv_s ;
-// logk], target = e1 * inv_s (inv_s read from device memory).
+// logk], target = e1 * inv_s / dinv (inv_s read from device memory).
 cudaError_t cnn_sample_glue(int which, long long n, const double* e0, const double* z, double* e1, const double* rp,
-                            const double* logk, const double* inv_s, float* in2, float* target, cudaStream_t st);
+                            const double* logk, const double* inv_s, const double* dinv, float* in2, float* target,
+                            cudaStream_t st);

@@ -48,6 +48,19 @@ cudaError_t cnn_forward_packed(const CnnDims& d, CnnWork& w, cudaStream_t st) {
   return e;
 }
 
+cudaError_t cnn_backward(const CnnDims& d, CnnWork& w, float* grad, cudaStream_t st) {
+  const size_t L = 27 * 256;
+  // layer 3: z3 = conv(a2); dz3 = g3
+  cudaError_t e = cnn_wgrad(d, w.a2, w.g3, w.part, 2, grad, st);
+  if (e == cudaSuccess) e = cnn_conv(d, CNN_EPI_MASK, 2, w.g3, w.pk.bwd + 2 * L, nullptr, w.a2, w.g2, st);
+  // layer 2: dz2 = conv3^T(dz3) * (a2 > 0)
+  if (e == cudaSuccess) e = cnn_wgrad(d, w.a1, w.g2, w.part, 1, grad, st);
+  if (e == cudaSuccess) e = cnn_conv(d, CNN_EPI_MASK, 2, w.g2, w.pk.bwd + L, nullptr, w.a1, w.g1, st);
+  // layer 1: dz1 = conv2^T(dz2) * (a1 > 0)
+  if (e == cudaSuccess) e = cnn_wgrad(d, w.a0, w.g1, w.part, 0, grad, st);
+  return e;
+}
+
 static int check_dims(const int dims[3], CnnDims& d) {
   if (!dims) return SMG_EINVAL;
   for (int t = 0; t < 3; ++t)
@@ -55,6 +68,8 @@ static int check_dims(const int dims[3], CnnDims& d) {
   d = CnnDims{dims[0], dims[1], dims[2]};
   return SMG_OK;
 }
+
+int cnn_check_dims(const int dims[3], CnnDims& d) { return check_dims(dims, d); }
 
 // ---- post-smoother glue (FP64 vectors, scalars in device memory) ----------
 namespace {
@@ -66,11 +81,11 @@ __global__ void k_inv_rms(const double* ss, double n, double* out) {
     out[1] = rms;
   }
 }
-// delta = s * y
+// delta = s * dinv * y
 __global__ void k_scale_out(long long n, const float* __restrict__ y, const double* __restrict__ s,
-                            double* __restrict__ delta) {
+                            const double* __restrict__ dinv, double* __restrict__ delta) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) delta[p] = s[0] * (double)y[p];
+  if (p < n) delta[p] = s[0] * dinv[p] * (double)y[p];
 }
 // z += delta when the corrected residual is smaller (ww < rr), else keep z
 __global__ void k_accept(long long n, double* __restrict__ z, const double* __restrict__ delta,
@@ -85,30 +100,67 @@ __global__ void k_sub(long long n, const double* __restrict__ a, const double* _
 }
 __global__ void k_sample_pack(long long n, const double* __restrict__ e1, const double* __restrict__ rp,
                               const double* __restrict__ logk, const double* __restrict__ inv_s,
-                              float* __restrict__ in2, float* __restrict__ target) {
+                              const double* __restrict__ dinv, float* __restrict__ in2, float* __restrict__ target) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const double is = inv_s[0];
   in2[p] = (float)(rp[p] * is);
   in2[n + p] = (float)logk[p];
-  target[p] = (float)(e1[p] * is);
+  target[p] = (float)(e1[p] * is / dinv[p]);
+}
+// q = t - in2[0..n)  (FP64)
+__global__ void k_resid_q(long long n, const double* __restrict__ t, const float* __restrict__ in2,
+                          double* __restrict__ q) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) q[p] = t[p] - (double)in2[p];
+}
+// loss += ss / n
+__global__ void k_loss_add(const double* __restrict__ ss, double n, float* __restrict__ loss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *loss += (float)(*ss / n);
+}
+// g3[p] = (bf16(2 dinv[p] t[p] / n), 0, ..., 0)
+__global__ void k_grad_out(long long n, const double* __restrict__ t, const double* __restrict__ dinv,
+                           __nv_bfloat16* __restrict__ g16) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const unsigned v = (unsigned)__bfloat16_as_ushort(__double2bfloat16(2.0 * dinv[p] * t[p] / (double)n));
+  reinterpret_cast<uint4*>(g16 + p * 16)[0] = make_uint4(v, 0, 0, 0);
+  reinterpret_cast<uint4*>(g16 + p * 16)[1] = make_uint4(0, 0, 0, 0);
+}
+// out = dinv * y (FP64)
+__global__ void k_scale_in(long long n, const float* __restrict__ y, const double* __restrict__ dinv,
+                           double* __restrict__ out) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) out[p] = dinv[p] * (double)y[p];
 }
 }  // namespace
 
+cudaError_t cnn_resid_glue(int which, long long n, const double* a, const float* f, const double* dinv, double* out,
+                           float* loss, __nv_bfloat16* g16, cudaStream_t st) {
+  const int nb = (int)((n + 255) / 256);
+  if (which == 0) k_resid_q<<<nb, 256, 0, st>>>(n, a, f, out);
+  else if (which == 1) k_loss_add<<<1, 32, 0, st>>>(a, (double)n, loss);
+  else if (which == 2) k_grad_out<<<nb, 256, 0, st>>>(n, a, dinv, g16);
+  else k_scale_in<<<nb, 256, 0, st>>>(n, f, dinv, out);
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
 cudaError_t cnn_sample_glue(int which, long long n, const double* e0, const double* z, double* e1, const double* rp,
-                            const double* logk, const double* inv_s, float* in2, float* target, cudaStream_t st) {
+                            const double* logk, const double* inv_s, const double* dinv, float* in2, float* target,
+                            cudaStream_t st) {
   const int nb = (int)((n + 255) / 256);
   if (which == 0) k_sub<<<nb, 256, 0, st>>>(n, e0, z, e1);
-  else k_sample_pack<<<nb, 256, 0, st>>>(n, e1, rp, logk, inv_s, in2, target);
+  else k_sample_pack<<<nb, 256, 0, st>>>(n, e1, rp, logk, inv_s, dinv, in2, target);
   smg_count_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t cnn_post_glue(int which, long long n, const float* y, double* z, double* delta, const double* a,
-                          const double* b, double* out, cudaStream_t st) {
+                          const double* b, const double* dinv, double* out, cudaStream_t st) {
   const int nb = (int)((n + 255) / 256);
   if (which == 0) k_inv_rms<<<1, 32, 0, st>>>(a, (double)n, out);
-  else if (which == 1) k_scale_out<<<nb, 256, 0, st>>>(n, y, a, delta);
+  else if (which == 1) k_scale_out<<<nb, 256, 0, st>>>(n, y, a, dinv, delta);
   else k_accept<<<nb, 256, 0, st>>>(n, z, delta, a, b);
   smg_count_launch(1);
   return cudaGetLastError();
@@ -155,14 +207,7 @@ extern "C" int smg_cnn_loss_grad(const int dims[3], const float* theta, const fl
   SMG_CUDA_TRY(cnn_forward_packed(d, w, st));
   const int nparts = (int)std::min<long long>(1024, (n + 255) / 256);
   SMG_CUDA_TRY(cnn_mse(n, w.y, target, w.g3, w.loss_part, nparts, loss, st));
-  // layer 3: z3 = conv(a2); dz3 = g3
-  SMG_CUDA_TRY(cnn_wgrad(d, w.a2, w.g3, w.part, 2, grad, st));
-  SMG_CUDA_TRY(cnn_conv(d, CNN_EPI_MASK, 2, w.g3, w.pk.bwd + 2 * L, nullptr, w.a2, w.g2, st));
-  // layer 2: dz2 = conv3^T(dz3) * (a2 > 0)
-  SMG_CUDA_TRY(cnn_wgrad(d, w.a1, w.g2, w.part, 1, grad, st));
-  SMG_CUDA_TRY(cnn_conv(d, CNN_EPI_MASK, 2, w.g2, w.pk.bwd + L, nullptr, w.a1, w.g1, st));
-  // layer 1: dz1 = conv2^T(dz2) * (a1 > 0)
-  SMG_CUDA_TRY(cnn_wgrad(d, w.a0, w.g1, w.part, 0, grad, st));
+  SMG_CUDA_TRY(cnn_backward(d, w, grad, st));
   return SMG_OK;
 }
 

@@ -92,10 +92,11 @@ constexpr int kDone = INT_MAX / 2;
 constexpr size_t kOneCtaPerSmSmem = 120 * 1024;
 constexpr unsigned kPublishGapNs = 300;
 // Shared ring of the last kRing values of every column.  A column's value
-// at point k is overwritten by point k + kRing, so a warp may run at most
-// kRing - SB - 2 steps ahead of its right-hand neighbour, which still has
-// to read the left column's values down to its point k - 1.
-constexpr int kRing = 8;
+// at point k is overwritten by point k + kRing.  A warp publishes step s
+// once point k is stored, before it reads the ring for point k+1, so its
+// left-hand neighbour may run at most kRing - SB - 2 steps ahead of the
+// published step without overwriting a value still to be read.
+constexpr int kRing = 16;
 
 __device__ __forceinline__ int ld_acq_cta(const int* p) {
   int v;
@@ -327,6 +328,10 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
             hp[(K & (kRing - 1)) * (NW * 32) + J] = r;
             carry = r;
           }
+          // -- point K is stored: publish step s before the loads of K+2 are
+          // issued, so the release does not wait for them
+          __syncwarp();
+          if (lane == 0) st_rel_cta(&sh.wdone[p][w], s + 1);
 
           // (2) partial sum of point K+1
           const int K1 = K + 1;
@@ -398,9 +403,6 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
               if (NS * sizeof(Val) > 128) prefetch_l2(pf + 128);
             }
           }
-          // -- this warp has finished step s
-          __syncwarp();
-          if (lane == 0) st_rel_cta(&sh.wdone[p][w], s + 1);
         }
         if (lane == 0) st_rel_cta(&sh.wdone[p][w], kDone);
       }

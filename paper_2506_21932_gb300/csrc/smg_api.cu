@@ -100,6 +100,7 @@ struct smg_ctx {
   void* ls_ws = nullptr;
   CnnWork ls_w{};
   double *ls_r = nullptr, *ls_d = nullptr, *ls_t = nullptr;
+  double* ls_dinv = nullptr;  // 1 / a_pp of the finest matrix: scales the network output
 };
 
 static int dev_alloc(smg_ctx* h, void** p, size_t bytes) {
@@ -244,7 +245,8 @@ static int coarse_solve(smg_ctx* h, const void* f, void* u, cudaStream_t st) {
 }
 
 // Learned post-smoother on the finest level (not in the paper), applied to
-// the V-cycle's result z: r' = r - A z, s = rms(r'), delta = s f(r'/s, logk),
+// the V-cycle's result z: r' = r - A z, s = rms(r'),
+// delta = s D^-1 f(r'/s, logk) with D the diagonal of A,
 // z += delta only if ||r' - A delta|| < ||r'||.  The decision is taken on the
 // device from the two norms; nothing is read back.
 static int learned_post_smooth(smg_ctx* h, const double* r, double* z, cudaStream_t st) {
@@ -254,13 +256,14 @@ static int learned_post_smooth(smg_ctx* h, const double* r, double* z, cudaStrea
   CnnDims d{L0.g.nx, L0.g.ny, L0.g.nz};
   SMG_CUDA_TRY(launch_spmv(A0, z, r, h->ls_r, 1, st));
   SMG_CUDA_TRY(kry_dot(n, h->ls_r, h->ls_r, h->sc, SC_LS_RR, h->rw, st));
-  SMG_CUDA_TRY(cnn_post_glue(0, n, nullptr, nullptr, nullptr, h->sc + SC_LS_RR, nullptr, h->sc + SC_LS_INVS, st));
+  SMG_CUDA_TRY(
+      cnn_post_glue(0, n, nullptr, nullptr, nullptr, h->sc + SC_LS_RR, nullptr, nullptr, h->sc + SC_LS_INVS, st));
   SMG_CUDA_TRY(cnn_pack_input(n, h->ls_r, h->ls_logk, h->sc + SC_LS_INVS, 0.0, h->ls_w.a0, st));
   SMG_CUDA_TRY(cnn_forward_packed(d, h->ls_w, st));
-  SMG_CUDA_TRY(cnn_post_glue(1, n, h->ls_w.y, nullptr, h->ls_d, h->sc + SC_LS_S, nullptr, nullptr, st));
+  SMG_CUDA_TRY(cnn_post_glue(1, n, h->ls_w.y, nullptr, h->ls_d, h->sc + SC_LS_S, nullptr, h->ls_dinv, nullptr, st));
   SMG_CUDA_TRY(launch_spmv(A0, h->ls_d, h->ls_r, h->ls_t, 1, st));
   SMG_CUDA_TRY(kry_dot(n, h->ls_t, h->ls_t, h->sc, SC_LS_WW, h->rw, st));
-  SMG_CUDA_TRY(cnn_post_glue(2, n, nullptr, z, h->ls_d, h->sc + SC_LS_WW, h->sc + SC_LS_RR, nullptr, st));
+  SMG_CUDA_TRY(cnn_post_glue(2, n, nullptr, z, h->ls_d, h->sc + SC_LS_WW, h->sc + SC_LS_RR, nullptr, nullptr, st));
   return SMG_OK;
 }
 
@@ -944,7 +947,7 @@ extern "C" int smg_level_apply(smg_t h, int l, int op, const void* x, const void
   return fetch_err(h, st);
 }
 
-static int ensure_ls_buffers(smg_ctx* h) {
+static int ensure_ls_buffers(smg_ctx* h, cudaStream_t st) {
   if (h->ls_ws) return SMG_OK;
   const Level& L0 = h->L[0];
   const long long n = L0.g.n;
@@ -953,15 +956,17 @@ static int ensure_ls_buffers(smg_ctx* h) {
   TRY(dalloc(h, &h->ls_r, n));
   TRY(dalloc(h, &h->ls_d, n));
   TRY(dalloc(h, &h->ls_t, n));
+  TRY(dalloc(h, &h->ls_dinv, n));
   cnn_carve(d, h->ls_ws, h->ls_w);
-  return SMG_OK;
+  SMG_CUDA_TRY(launch_diag_inverse(L0.g, L0.s, 1, L0.A, h->ls_dinv, h->err, st));
+  return fetch_err(h, st);
 }
 
 extern "C" int smg_learned_sample(smg_t h, const double* e0, const double* logk, float* in2, float* target,
                                   void* stream) {
   if (!h || !e0 || !logk || !in2 || !target || h->B != 1) return SMG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  TRY(ensure_ls_buffers(h));
+  TRY(ensure_ls_buffers(h, st));
   const Level& L0 = h->L[0];
   const long long n = L0.g.n;
   const LevelView A0 = view(h, L0, false);
@@ -971,12 +976,45 @@ extern "C" int smg_learned_sample(smg_t h, const double* e0, const double* logk,
   const int rc = vcycle_body(h, h->ls_r, h->ls_d, st);
   h->ls_logk = saved;
   TRY(rc);
-  SMG_CUDA_TRY(cnn_sample_glue(0, n, e0, h->ls_d, h->ls_t, nullptr, nullptr, nullptr, nullptr, nullptr, st));
+  SMG_CUDA_TRY(cnn_sample_glue(0, n, e0, h->ls_d, h->ls_t, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, st));
   SMG_CUDA_TRY(launch_spmv(A0, h->ls_t, h->ls_t, h->ls_r, 0, st));  // r' = A e1
   SMG_CUDA_TRY(kry_dot(n, h->ls_r, h->ls_r, h->sc, SC_LS_RR, h->rw, st));
-  SMG_CUDA_TRY(cnn_post_glue(0, n, nullptr, nullptr, nullptr, h->sc + SC_LS_RR, nullptr, h->sc + SC_LS_INVS, st));
-  SMG_CUDA_TRY(cnn_sample_glue(1, n, nullptr, nullptr, h->ls_t, h->ls_r, logk, h->sc + SC_LS_INVS, in2, target, st));
+  SMG_CUDA_TRY(
+      cnn_post_glue(0, n, nullptr, nullptr, nullptr, h->sc + SC_LS_RR, nullptr, nullptr, h->sc + SC_LS_INVS, st));
+  SMG_CUDA_TRY(cnn_sample_glue(1, n, nullptr, nullptr, h->ls_t, h->ls_r, logk, h->sc + SC_LS_INVS, h->ls_dinv, in2,
+                               target, st));
   return fetch_err(h, st);
+}
+
+extern "C" int smg_learned_loss_grad(smg_t h, const float* theta, const float* in2, const float* target, int kind,
+                                     float* grad, float* loss, void* ws, size_t ws_bytes, void* stream) {
+  if (!h || !theta || !in2 || !grad || !loss || !ws || h->B != 1) return SMG_EINVAL;
+  if (kind != SMG_LOSS_ERROR && kind != SMG_LOSS_RESIDUAL) return SMG_EINVAL;
+  const Level& L0 = h->L[0];
+  const int dims[3] = {L0.g.nx, L0.g.ny, L0.g.nz};
+  if (kind == SMG_LOSS_ERROR) return smg_cnn_loss_grad(dims, theta, in2, target, grad, loss, ws, ws_bytes, stream);
+  CnnDims d{L0.g.nx, L0.g.ny, L0.g.nz};
+  if (ws_bytes < cnn_workspace_bytes(d)) return SMG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  TRY(ensure_ls_buffers(h, st));
+  const long long n = L0.g.n;
+  const LevelView A0 = view(h, L0, false);
+  CnnWork w;
+  cnn_carve(d, ws, w);
+  SMG_CUDA_TRY(cnn_pack(theta, w.pk, st));
+  SMG_CUDA_TRY(cnn_pack_input_f32(n, in2, w.a0, st));
+  SMG_CUDA_TRY(cnn_forward_packed(d, w, st));
+  // q = A D^-1 y - rhat, loss += |q|^2 / n, output gradient 2 D^-1 A q / n
+  // (A symmetric, D its diagonal)
+  SMG_CUDA_TRY(cnn_resid_glue(3, n, nullptr, w.y, h->ls_dinv, h->ls_d, nullptr, nullptr, st));
+  SMG_CUDA_TRY(launch_spmv(A0, h->ls_d, h->ls_d, h->ls_t, 0, st));
+  SMG_CUDA_TRY(cnn_resid_glue(0, n, h->ls_t, in2, nullptr, h->ls_r, nullptr, nullptr, st));
+  SMG_CUDA_TRY(kry_dot(n, h->ls_r, h->ls_r, h->sc, SC_LS_RR, h->rw, st));
+  SMG_CUDA_TRY(cnn_resid_glue(1, n, h->sc + SC_LS_RR, nullptr, nullptr, nullptr, loss, nullptr, st));
+  SMG_CUDA_TRY(launch_spmv(A0, h->ls_r, h->ls_r, h->ls_t, 0, st));
+  SMG_CUDA_TRY(cnn_resid_glue(2, n, h->ls_t, nullptr, h->ls_dinv, nullptr, nullptr, w.g3, st));
+  SMG_CUDA_TRY(cnn_backward(d, w, grad, st));
+  return SMG_OK;
 }
 
 extern "C" int smg_set_learned_smoother(smg_t h, const float* theta, const double* logk, void* stream) {
@@ -991,7 +1029,7 @@ extern "C" int smg_set_learned_smoother(smg_t h, const float* theta, const doubl
     return SMG_OK;
   }
   if (!logk || h->B != 1 || h->opt.krylov == SMG_KRYLOV_PCG) return SMG_EINVAL;
-  TRY(ensure_ls_buffers(h));
+  TRY(ensure_ls_buffers(h, st));
   SMG_CUDA_TRY(cnn_pack(theta, h->ls_w.pk, st));
   h->ls_logk = logk;
   // a captured V-cycle graph does not contain the post-smoother yet

@@ -4,8 +4,10 @@ and the Adam update all run in the library's kernels).
 
 Each training pair comes from a known error: e0 ~ N(0, 1) iid on the finest
 grid, r0 = A e0, e1 = e0 - V(r0) is the error one V-cycle leaves, and the
-network learns delta ~ e1 from (r' = A e1, log kappa), both scaled by
-s = rms(r').  The Gaussian draws are the only random numbers; they come from
+network learns a correction delta ~ e1 from (r' = A e1, log kappa), both
+scaled by s = rms(r').  The default loss measures delta by the residual it
+leaves, |r' - A delta|^2 (the quantity the post-smoother's acceptance test
+compares); the plain error MSE |delta - e1|^2 is the alternative.  The Gaussian draws are the only random numbers; they come from
 a seeded device generator and enter the library as inputs.
 """
 import torch
@@ -22,9 +24,9 @@ class PostSmootherTrainer:
     that grid (float64 device tensor), or the matching list.  Samples cycle
     through the fields in order."""
 
-    def __init__(self, mg, logk, seed=0, lr=1e-3, batch=4, theta=None, stream=None):
+    def __init__(self, mg, logk, seed=0, lr=1e-3, batch=4, theta=None, loss_kind=S.LOSS_RESIDUAL, stream=None):
         self.fields = list(zip(mg, logk)) if isinstance(mg, (list, tuple)) else [(mg, logk)]
-        self.lr, self.batch = lr, int(batch)
+        self.lr, self.batch, self.loss_kind = lr, int(batch), loss_kind
         mg, logk = self.fields[0]
         assert all(tuple(m.dims) == tuple(mg.dims) for m, _ in self.fields)
         self.nsamples = 0
@@ -47,11 +49,16 @@ class PostSmootherTrainer:
         self.stream = stream
 
     def sample(self):
-        """Draws e0 and builds one training pair into (in2, target)."""
+        """Draws e0 and builds one training pair into (in2, target); returns
+        the hierarchy it came from."""
         mg, logk = self.fields[self.nsamples % len(self.fields)]
         self.nsamples += 1
         self.e0.normal_(generator=self.gen)
         mg.learned_sample(self.e0, logk, self.in2, self.target, self.stream)
+        return mg
+
+    def _loss_grad(self, mg, grad, loss):
+        mg.learned_loss_grad(self.theta, self.in2, self.target, grad, loss, self.ws, self.loss_kind, self.stream)
 
     def step(self):
         """One Adam step on a fresh batch; returns the batch's mean loss as a
@@ -59,8 +66,7 @@ class PostSmootherTrainer:
         self.grad.zero_()
         self.loss.zero_()
         for _ in range(self.batch):
-            self.sample()
-            S.cnn_loss_grad(self.dims, self.theta, self.in2, self.target, self.grad, self.loss, self.ws, self.stream)
+            self._loss_grad(self.sample(), self.grad, self.loss)
         self.t += 1
         S.cnn_adam(self.theta, self.m, self.v, self.grad, self.t, lr=self.lr, grad_scale=1.0 / self.batch,
                    stream=self.stream)
@@ -71,8 +77,7 @@ class PostSmootherTrainer:
         scratch = torch.zeros_like(self.grad)
         loss = torch.zeros(1, dtype=torch.float32, device=self.theta.device)
         for _ in range(samples):
-            self.sample()
-            S.cnn_loss_grad(self.dims, self.theta, self.in2, self.target, scratch, loss, self.ws, self.stream)
+            self._loss_grad(self.sample(), scratch, loss)
         return float(loss.item()) / samples
 
     def train(self, steps):

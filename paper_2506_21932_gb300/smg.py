@@ -19,6 +19,7 @@ PCG, FPCG, FGMRES = 0, 1, 2
 OP_SPMV, OP_RESIDUAL, OP_GS_FORWARD, OP_GS_BACKWARD, OP_GS_ZERO, OP_ILU_APPLY, OP_RESTRICT, OP_PROLONG_ADD, \
     OP_COARSE_SOLVE, OP_ILU_LOWER, OP_ILU_UPPER = range(11)
 ARR_A, ARR_LU, ARR_DINV, ARR_AV, ARR_AS, ARR_LUV, ARR_LS, ARR_US, ARR_DINV32 = range(9)
+LOSS_ERROR, LOSS_RESIDUAL = 0, 1
 
 _lib = None
 
@@ -77,6 +78,7 @@ def lib():
         L.smg_cnn_adam.argtypes = [i, vp, vp, vp, vp, i, f, f, f, f, f, vp]
         L.smg_set_learned_smoother.argtypes = [vp, vp, vp, vp]
         L.smg_learned_sample.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.smg_learned_loss_grad.argtypes = [vp, vp, vp, vp, i, vp, vp, vp, ctypes.c_size_t, vp]
         _lib = L
     return _lib
 
@@ -264,6 +266,14 @@ class SMG:
         rc = self._lib.smg_learned_sample(self.h, _ptr(e0), _ptr(logk), _ptr(in2), _ptr(target), _stream(stream))
         if rc != OK:
             raise SmgError(rc, "smg_learned_sample")
+
+    def learned_loss_grad(self, theta, in2, target, grad, loss, ws, kind=1, stream=None):
+        """Accumulates the loss (LOSS_ERROR or LOSS_RESIDUAL) and its gradient
+        for one training pair on this hierarchy's finest grid."""
+        rc = self._lib.smg_learned_loss_grad(self.h, _ptr(theta), _ptr(in2), _ptr(target), int(kind), _ptr(grad),
+                                             _ptr(loss), _ptr(ws), ws.numel(), _stream(stream))
+        if rc != OK:
+            raise SmgError(rc, "smg_learned_loss_grad")
 
     def selftest_wait(self, budget_ms=20, stream=None):
         """Runs one bounded device wait that must time out; returns the status."""

@@ -106,7 +106,8 @@ def test_flat_parameter_layout_round_trips():
 
 def test_identity_network_solves_a_diagonal_system_exactly():
     """With A = c I the exact error is r'/c; the identity network scaled by
-    1/c yields it, so the step is accepted and z becomes A^-1 r."""
+    1/c yields it, so the step is accepted and z becomes A^-1 r.  With the
+    Jacobi scaling dinv = 1/c the unscaled identity network does the same."""
     rng = np.random.default_rng(6)
     dims = (4, 5, 6)
     c = 3.0
@@ -115,6 +116,9 @@ def test_identity_network_solves_a_diagonal_system_exactly():
     logk = rng.normal(size=dims)
     A = lambda v: c * v
     znew, ok = C.post_smooth(A, r, z, logk, C.identity_network(1.0 / c))
+    assert ok
+    assert np.max(np.abs(znew - r / c)) < 1e-13
+    znew, ok = C.post_smooth(A, r, z, logk, C.identity_network(1.0), dinv=np.full(r.size, 1.0 / c))
     assert ok
     assert np.max(np.abs(znew - r / c)) < 1e-13
 
@@ -142,3 +146,76 @@ def test_training_pair_of_an_exact_solver_is_zero():
     # e1 = -1e-3 noise, r' = 2 e1, s = rms(r'); target = e1 / s has rms 1/2
     assert abs(np.sqrt(np.mean(t ** 2)) - 0.5) < 1e-12
     assert np.allclose(x[0].ravel(), 2.0 * t.ravel())
+
+
+def test_residual_loss_with_a_scaled_identity_is_a_scaled_mse():
+    """A = c I: loss = mean((c y - rhat)^2) = c^2 mean((y - rhat/c)^2), and
+    its gradients are c^2 times those of the MSE against rhat / c."""
+    rng = np.random.default_rng(9)
+    params = C.init_params(seed=10)
+    x = rng.normal(size=(2, 5, 4, 6))
+    c = 1.7
+    lr_, gr = C.residual_loss_and_grads(params, x, lambda v: c * v)
+    lm, gm = C.mse_loss_and_grads(params, x, x[:1] / c)
+    assert abs(lr_ - c * c * lm) < 1e-12 * lr_
+    for (a, b), (e, f) in zip(gr, gm):
+        assert np.max(np.abs(a - c * c * e)) < 1e-12 * max(1.0, np.max(np.abs(a)))
+        assert np.max(np.abs(b - c * c * f)) < 1e-12 * max(1.0, np.max(np.abs(b)))
+
+
+def test_residual_loss_gradients_match_central_differences():
+    """A = a symmetric positive 7-point operator on the 5x5x5 grid."""
+    rng = np.random.default_rng(11)
+    dims = (5, 5, 5)
+    params = C.init_params(seed=12)
+    x = rng.normal(size=(2,) + dims)
+
+    def A(v):
+        u = v.reshape(dims)
+        out = 8.0 * u
+        for ax in range(3):
+            for sh in (-1, 1):
+                out -= C.shifted(u[None], tuple(sh if a == ax else 0 for a in range(3)))[0]
+        return out.reshape(-1)
+
+    loss, grads = C.residual_loss_and_grads(params, x, A)
+    h = 1e-6
+    for l in range(3):
+        W = params[l][0]
+        for idx in [(0, 0, 1, 1, 1), (W.shape[0] - 1, W.shape[1] - 1, 2, 0, 1)]:
+            def L(delta):
+                P = [(w.copy(), bb.copy()) for w, bb in params]
+                P[l][0][idx] += delta
+                return C.residual_loss_and_grads(P, x, A)[0]
+            fd = (L(h) - L(-h)) / (2 * h)
+            assert abs(grads[l][0][idx] - fd) <= 1e-6 * max(1e-3, abs(fd)), (l, idx)
+
+
+def test_residual_loss_with_jacobi_scaling_of_a_diagonal_matrix_is_the_mse():
+    """A = diag(d) with dinv = 1/d: A (dinv y) = y, so the residual loss is
+    the MSE of y against rhat and the gradients agree with it."""
+    rng = np.random.default_rng(13)
+    dims = (4, 5, 3)
+    params = C.init_params(seed=14)
+    x = rng.normal(size=(2,) + dims)
+    d = rng.uniform(0.5, 3.0, size=np.prod(dims))
+    lr_, gr = C.residual_loss_and_grads(params, x, lambda v: d * v, dinv=1.0 / d)
+    lm, gm = C.mse_loss_and_grads(params, x, x[:1])
+    assert abs(lr_ - lm) < 1e-12 * lm
+    for (a, b), (e, f) in zip(gr, gm):
+        assert np.max(np.abs(a - e)) < 1e-12 * max(1.0, np.max(np.abs(a)))
+        assert np.max(np.abs(b - f)) < 1e-12 * max(1.0, np.max(np.abs(b)))
+
+
+def test_training_target_reproduces_the_error_through_the_jacobi_scaling():
+    rng = np.random.default_rng(15)
+    dims = (3, 4, 5)
+    n = int(np.prod(dims))
+    diag = rng.uniform(1.0, 4.0, size=n)
+    A = lambda v: diag * v + 0.1 * np.roll(v, 1) + 0.1 * np.roll(v, -1)
+    e0 = rng.normal(size=n)
+    vc = lambda rr: rr / diag
+    x, t = C.training_pair(A, vc, e0, np.zeros(dims), diag=diag)
+    e1 = e0 - vc(A(e0))
+    s = np.sqrt(np.mean(A(e1) ** 2))
+    assert np.allclose(s * t.ravel() / diag, e1, rtol=1e-13, atol=1e-15)

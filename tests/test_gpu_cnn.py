@@ -175,10 +175,46 @@ def test_training_pair_matches_oracle(S, C, orc):
     in2 = torch.empty(2 * n, dtype=torch.float32, device="cuda")
     tgt = torch.empty(n, dtype=torch.float32, device="cuda")
     h.learned_sample(cu(e0), cu(logk), in2, tgt)
-    xr, tr = C.training_pair(lambda v: orc.spmv(d, I.OFF7, A, v), mg.vcycle, e0, logk.reshape(d))
+    diag = A[:, I.OFF7.index((0, 0, 0))]
+    xr, tr = C.training_pair(lambda v: orc.spmv(d, I.OFF7, A, v), mg.vcycle, e0, logk.reshape(d), diag=diag)
     assert rel_max(in2.cpu().numpy()[:n], xr[0].ravel()) < 1e-6
     assert np.array_equal(in2.cpu().numpy()[n:], logk.astype(np.float32))
     assert rel_max(tgt.cpu().numpy(), tr.ravel()) < 1e-6
+
+
+def test_residual_loss_and_gradients_match_oracle(S, C, orc):
+    """Loss |A y - r'/s|^2 / n on the context's finest matrix and its
+    gradient, against the oracle in its BF16-rounding mode (the A products
+    amplify the network's rounding differences by the spread of A's
+    eigenvalues, hence twice the forward tolerance)."""
+    d = (16, 16, 16)
+    A, logk = varcoef(d, 7)
+    n = A.shape[0]
+    h = S.SMG(d, I.OFF7, cu(A), smoother=S.SGS, krylov=S.FPCG)
+    theta = I.cnn_theta(5)
+    theta[880 - 16:880] = 0.03
+    x = I.cnn_volume(d, 2, seed=8)
+    x[1] = torch.from_numpy(logk.astype(np.float32))
+    ws = S.cnn_workspace(d)
+    grad = torch.zeros(I.CNN_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    h.learned_loss_grad(cu(theta.numpy()), cu(x.numpy()), None, grad, loss, ws, kind=S.LOSS_RESIDUAL)
+    torch.cuda.synchronize()
+    params = C.unflatten(theta.numpy())
+    xo = x.numpy().astype(np.float64).reshape((2,) + d)
+    dinv = 1.0 / A[:, I.OFF7.index((0, 0, 0))]
+    lref, gref = C.residual_loss_and_grads(params, xo, lambda v: orc.spmv(d, I.OFF7, A, v), bf=True, dinv=dinv)
+    assert abs(loss.item() - lref) <= 2 * TOL_EMU * lref
+    g = grad.cpu().numpy().astype(np.float64)
+    gflat = C.flatten(gref)
+    o = 0
+    for l, (W, b) in enumerate(params):
+        nw = W.size
+        assert rel2(g[o:o + nw], gflat[o:o + nw]) < 4 * TOL_EMU, (l, "W")
+        assert rel2(g[o + nw:o + nw + b.size], gflat[o + nw:o + nw + b.size]) < 4 * TOL_EMU, (l, "b")
+        o += nw + b.size
+    with pytest.raises(S.SmgError):
+        h.learned_loss_grad(cu(theta.numpy()), cu(x.numpy()), None, grad, loss, ws, kind=7)
 
 
 def test_post_smoother_matches_oracle_when_accepted_and_rejected(S, C, orc):
@@ -192,15 +228,18 @@ def test_post_smoother_matches_oracle_when_accepted_and_rejected(S, C, orc):
     z_plain = torch.empty(n, dtype=torch.float64, device="cuda")
     h.vcycle(cu(r), z_plain)
     zo = mg.vcycle(r)
-    # (1) a Richardson step delta = g r' with g below 1/lambda_max: accepted
-    gain = 0.5 / A[:, I.OFF7.index((0, 0, 0))].max()
+    # (1) a damped Jacobi step delta = 0.3 D^-1 r' (the identity network
+    #     times 0.3 through the Jacobi scaling): accepted
+    dinv = 1.0 / A[:, I.OFF7.index((0, 0, 0))]
+    gain = 0.3
     params = C.identity_network(gain)
     theta = cu(C.flatten(params).astype(np.float32))
     lk = cu(logk)
     h.set_learned_smoother(theta, lk)
     z = torch.empty(n, dtype=torch.float64, device="cuda")
     h.vcycle(cu(r), z)
-    zref, ok = C.post_smooth(Aop, r, zo, logk.reshape(d), C.unflatten(C.flatten(params).astype(np.float32)), bf=True)
+    zref, ok = C.post_smooth(Aop, r, zo, logk.reshape(d), C.unflatten(C.flatten(params).astype(np.float32)), bf=True,
+                             dinv=dinv)
     assert ok
     assert rel2(z.cpu().numpy(), zref) < 1e-6
     assert rel2(z.cpu().numpy(), z_plain.cpu().numpy()) > 1e-6  # the step changed z
@@ -225,17 +264,22 @@ def test_learned_smoother_requires_a_flexible_krylov_method(S):
 
 def test_training_lowers_the_loss_and_the_iteration_count(S):
     """Trains on 32^3 problems of the variable-coefficient family (training
-    seed), then solves a problem of another seed with FPCG and the learned
+    seeds), then solves a problem of another seed with FPCG and the learned
     post-smoother, against FPCG with the plain V-cycle."""
     from paper_2506_21932_gb300.learned import PostSmootherTrainer
     d = (32, 32, 32)
-    A, logk = varcoef(d, 1000)
-    h = S.SMG(d, I.OFF7, cu(A), smoother=S.SGS, krylov=S.FPCG)
-    tr = PostSmootherTrainer(h, cu(logk), seed=0, lr=2e-3, batch=4)
+    hs, lks = [], []
+    for seed in (1000, 1001, 1002, 1003):
+        A, logk = varcoef(d, seed)
+        hs.append(S.SMG(d, I.OFF7, cu(A), smoother=S.SGS, krylov=S.FPCG))
+        lks.append(cu(logk))
+    tr = PostSmootherTrainer(hs, lks, seed=0, lr=2e-3, batch=4)
     before = tr.eval_loss(8)
     tr.train(150)
     after = tr.eval_loss(8)
-    assert after < 0.8 * before, (before, after)
+    print("residual loss %.4g -> %.4g" % (before, after))
+    # below 1: on average the correction leaves a smaller residual than r'
+    assert after < 0.8 * before and after < 1.0, (before, after)
 
     A2, logk2 = varcoef(d, 0)
     n = A2.shape[0]
