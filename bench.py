@@ -390,15 +390,19 @@ def oracle_sample(w, seed=0):
     A, b = A.numpy(), b.numpy()
     B = w.get("block", 1)
     t0 = time.perf_counter()
+    # the oracle's reduced-precision cycles are scalar only: a block workload
+    # is timed with its FP64 hierarchy
+    prec = w["precision"] if B == 1 else 0
     mg = orc.MG(sd, off, A.reshape(A.shape[0], -1) if B == 1 else A, B=B, smoother=w["smoother"],
-                transfer=w["transfer"], precision=w["precision"])
+                transfer=w["transfer"], precision=prec)
     if w["krylov"] == 2:
         x, rc, it, rr, _ = mg.fgmres(b, tol=w["tol"], restart=30, maxit=1000)
     else:
         x, rc, it, rr, _ = mg.pcg(b, tol=w["tol"], maxit=1000, flexible=w["krylov"] == 1)
     t = time.perf_counter() - t0
     scale = full / (sd[0] * sd[1] * sd[2])
-    return dict(value=t * scale, raw_s=t, scale=scale, grid=sd, iters=it, relres=rr, rc=rc)
+    return dict(value=t * scale, raw_s=t, scale=scale, grid=sd, iters=it, relres=rr, rc=rc,
+                fp64_hierarchy=prec != w["precision"])
 
 
 def main():
@@ -454,6 +458,8 @@ def main():
                    "x".join(map(str, o["grid"])), o["scale"], o["iters"], o["scale"])}
         if w.get("learned"):
             cpu["sample"] += "; plain V-cycle (the timed oracle runs no network)"
+        if o.get("fp64_hierarchy"):
+            cpu["sample"] += "; FP64 hierarchy (the oracle has no reduced-precision block cycle)"
     s = r["stats"]
     line = {"metric": metric, "value": round(r["ms"] / 1e3, 5), "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(r["ms"], 3), "higher_is_better": False, "scaling": "weak",

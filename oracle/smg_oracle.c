@@ -613,14 +613,15 @@ void orc_mg_free(void* h) {
 /* Build the hierarchy: Galerkin coarse operators by orc_rap27 (kept on the
  * offsets a chain reaches, in lexicographic order), smoother set-up on every
  * non-coarsest level, dense LU of the coarsest.  precision: 0 FP64, 1 FP32,
- * 2 BF16 with row scales (scalar problems only). */
+ * 2 BF16 with row scales; the reduced-precision cycles exist for scalar
+ * problems only (B == 1), other combinations are rejected. */
 int orc_mg_setup(void** out, const int d[3], int ns, const int* off, int B, const double* A, int smoother,
                  int transfer, double w, int precision, int max_levels) {
   *out = NULL;
   if (orc_mask_validate(ns, off)) return ORC_EINVAL;
   if (B != 1 && B != 3) return ORC_EINVAL;
   if (B == 3 && smoother != SM_SGS) return ORC_EINVAL;
-  if (precision == 2 && B != 1) return ORC_EINVAL;
+  if (precision != 0 && B != 1) return ORC_EINVAL;
   for (int t = 0; t < 3; ++t)
     if (d[t] < 1) return ORC_EINVAL;
   orc_mg* mg = (orc_mg*)calloc(1, sizeof(orc_mg));

@@ -301,6 +301,8 @@ cudaError_t launch_sweep(const LevelView& L, int kind, int dir, const void* M, c
   const int nthr = sweep_threads(L.g);
   const int grid = L.g.nx;
   if (L.B == 3) {
+    cudaError_t eb = launch_bsweep3(L, kind, dir, M, dinv, w, b, u, ws, err, cfg, st);
+    if (eb != cudaErrorNotSupported) return eb;
 #define S3(V, KD, DR) k_sweep3<V, KD, DR><<<grid, nthr, 0, st>>>(P)
     if (L.pk == K64) {
       if (kind == SW_GS_ZERO) S3(double, SW_GS_ZERO, 1);
@@ -343,6 +345,8 @@ cudaError_t launch_ilu_factor(Grid g, const Stencil& s, const double* A, double*
   (void)nupd;
   cudaError_t e = cudaMemcpyAsync(LU, A, sizeof(double) * g.n * s.ns, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
+  e = launch_ilu_factor3(g, s, LU, udinv, ws, err, cfg.budget_ns, st);
+  if (e != cudaErrorNotSupported) return e;
   IluParams Q;
   Q.base.g = g;
   Q.base.s = s;

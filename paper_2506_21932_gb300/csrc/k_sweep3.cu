@@ -29,33 +29,10 @@
 #include <algorithm>
 #include <climits>
 
+#include "shapes.cuh"
 #include "smg_internal.cuh"
 
 namespace {
-
-template <int NS> struct Shape;
-template <> struct Shape<27> {
-  static constexpr int SA = 4, SB = 2, EC = 13;
-  __host__ __device__ static constexpr int o(int e, int d) {
-    return d == 0 ? e / 9 - 1 : (d == 1 ? (e / 3) % 3 - 1 : e % 3 - 1);
-  }
-};
-template <> struct Shape<7> {
-  static constexpr int SA = 1, SB = 1, EC = 3;
-  __host__ __device__ static constexpr int o(int e, int d) {
-    return d == 0 ? (e == 0 ? -1 : (e == 6 ? 1 : 0)) : d == 1 ? (e == 1 ? -1 : (e == 5 ? 1 : 0))
-                                                               : (e == 2 ? -1 : (e == 4 ? 1 : 0));
-  }
-};
-template <> struct Shape<19> {
-  static constexpr int SA = 3, SB = 2, EC = 9;
-  __host__ __device__ static constexpr int o(int e, int d) {
-    constexpr int t[19][3] = {{-1, -1, 0}, {-1, 0, -1}, {-1, 0, 0}, {-1, 0, 1}, {-1, 1, 0}, {0, -1, -1}, {0, -1, 0},
-                              {0, -1, 1},  {0, 0, -1},  {0, 0, 0},  {0, 0, 1},  {0, 1, -1}, {0, 1, 0},   {0, 1, 1},
-                              {1, -1, 0},  {1, 0, -1},  {1, 0, 0},  {1, 0, 1},  {1, 1, 0}};
-    return t[e][d];
-  }
-};
 
 enum { C_SKIP = 0, C_OWN = 1, C_LATE = 2, C_EARLY = 3, C_MEM = 4 };
 
@@ -106,7 +83,6 @@ __device__ __forceinline__ int ld_acq_cta(const int* p) {
 __device__ __forceinline__ void st_rel_cta(int* p, int v) {
   asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
 }
-__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 template <int W>
@@ -190,19 +166,18 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
       }
     } else if (warp == ncompute + 1) {
       // ---- poller warp: lane w forwards the progress of warp w of the
-      // previous CTA's last plane into shared memory (relaxed polls, one
-      // GPU-scope acquire fence per batch of new values)
+      // previous CTA's last plane into shared memory (GPU-scope acquire loads)
       const bool mine = lane < NW;
       const int* in_slot = P.ws->prog + (size_t)(I - 1) * NW + lane;
       int seen = (I == 0 || !mine) ? kDone : 0;
       unsigned long long t_wait = 0;
       unsigned iter = 0;
       while (__any_sync(0xffffffffu, seen < kDone)) {
-        const int v = seen < kDone ? ld_relaxed(in_slot) : seen;
+        int v = seen;
+        if (seen < kDone) asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(in_slot) : "memory");
         const bool fresh = v > seen;
         bool stop = false;
         if (__any_sync(0xffffffffu, fresh)) {
-          fence_acq_rel_gpu();
           if (fresh) {
             seen = v;
             st_rel_cta(&sh.avail[lane], v);

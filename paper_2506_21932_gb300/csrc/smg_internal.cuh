@@ -188,6 +188,17 @@ cudaError_t launch_wait_selftest(const int* flag, int* err, unsigned long long b
 
 // ILU(0) factorisation (FP64, wavefront over the lower dependencies).
 // upd: [kstart (ec+1 ints, padded to an even count)] then int2 pairs.
+// Point-block (B == 3) Gauss-Seidel sweeps (GS_ZERO / GS_FULL) on the
+// per-warp wavefront engine, for the canonical 7/19/27-point masks, FP64 or
+// FP32, ny <= 512; cudaErrorNotSupported (nothing launched) otherwise.
+cudaError_t launch_bsweep3(const LevelView& L, int kind, int dir, const void* M, const void* dinv, double w,
+                           const void* b, void* u, SweepWs* ws, int* err, const SweepCfg& cfg, cudaStream_t st);
+// ILU(0) factorisation of LU in place (LU holds A on entry) on the
+// warp-pipelined wavefront, for the canonical 7/19/27-point masks with one
+// unknown per point and ny <= 512; cudaErrorNotSupported (nothing launched)
+// otherwise.
+cudaError_t launch_ilu_factor3(Grid g, const Stencil& s, double* LU, double* udinv, SweepWs* ws, int* err,
+                               unsigned long long budget_ns, cudaStream_t st);
 cudaError_t launch_ilu_factor(Grid g, const Stencil& s, const double* A, double* LU, double* udinv,
                               const int* upd, int nupd, SweepWs* ws, int* err, const SweepCfg& cfg, cudaStream_t st);
 

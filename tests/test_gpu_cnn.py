@@ -291,6 +291,20 @@ def test_training_lowers_the_loss_and_the_iteration_count(S):
     learned.set_learned_smoother(tr.theta, cu(logk2))
     x.zero_()
     it_l, rr_l, _ = learned.solve(b, x, tol=1e-9, maxit=200)
-    print("loss %.4g -> %.4g; FPCG iterations plain %d, learned %d" % (before, after, it_plain, it_l))
+    # what one preconditioner application leaves of a random residual
+    ratios = {}
+    for name, h in (("plain", plain), ("learned", learned)):
+        acc = []
+        for seed in range(3):
+            r = cu(np.random.default_rng(100 + seed).normal(size=n))
+            z = torch.empty_like(r)
+            h.vcycle(r, z)
+            t = torch.empty_like(r)
+            h.level_apply(0, S.OP_RESIDUAL, x=z, b=r, y=t)
+            acc.append(float(t.norm() / r.norm()))
+        ratios[name] = sum(acc) / len(acc)
+    print("loss %.4g -> %.4g; residual left by one application: plain %.4g, learned %.4g; FPCG iterations "
+          "plain %d, learned %d" % (before, after, ratios["plain"], ratios["learned"], it_plain, it_l))
     assert rr_l < 1e-9 and rr_plain < 1e-9
+    assert ratios["learned"] < 0.8 * ratios["plain"]
     assert it_l <= it_plain

@@ -138,8 +138,8 @@ def test_gs_sweeps_on_small_odd_grids(S, orc):
         assert rel_max(host(u), orc.gs_forward(d, off, A, Dinv, b, np.zeros_like(b))) < TOL_KERNEL
 
 
-def test_block_gs_sweeps(S, orc):
-    d = (8, 10, 8)
+@pytest.mark.parametrize("d", [(8, 10, 8), (8, 70, 10), (8, 34, 8)])
+def test_block_gs_sweeps(S, orc, d):
     A = I.block7_layered(d, 2).numpy()
     h = make(S, d, I.OFF7, A, block=3, transfer=S.PC8C, smoother=S.SGS, max_levels=2)
     Dinv = orc.diag_inverse(d, I.OFF7, A, B=3)
@@ -302,6 +302,27 @@ def test_fgmres_block_solve_matches_oracle(S, orc):
     xr, rcr, itr, rrr, _ = ref.fgmres(b, tol=1e-8, restart=30, maxit=300)
     assert rc == 0 and rcr == 0 and abs(it - itr) <= 1 and rr < 1e-8
     res = np.linalg.norm(orc.residual(d, I.OFF7, A, b, host(x), B=3)) / np.linalg.norm(b)
+    assert res < 1e-8
+
+
+def test_fp32_block_hierarchy_vcycle_and_fgmres(S, orc):
+    """The 3-unknown system with an FP32 hierarchy (block GS in float).  The
+    oracle has no reduced-precision block cycle, so the V-cycle is held to the
+    FP64 oracle's within FP32 accuracy (unit roundoff 6e-8 grown over the
+    cycle's sweeps and transfers: 1e-4), and the FGMRES solve must reach the
+    tolerance with the true residual recomputed by the oracle."""
+    d = (16, 16, 8)
+    A = I.block7_layered(d, 7).numpy()
+    r = I.rhs(np.prod(d) * 3, 12).numpy()
+    h = make(S, d, I.OFF7, A, block=3, transfer=S.PC8C, precision=S.FP32, krylov=S.FGMRES, restart=30)
+    z = torch.empty_like(cu(r))
+    h.vcycle(cu(r), z)
+    ref = orc.MG(d, I.OFF7, A, B=3, transfer=orc.PC8C)
+    assert rel2(host(z), ref.vcycle(r)) < 1e-4
+    x = torch.zeros_like(cu(r))
+    it, rr, rc = h.solve(cu(r), x, tol=1e-8, maxit=300)
+    assert rc == 0 and rr < 1e-8
+    res = np.linalg.norm(orc.residual(d, I.OFF7, A, r, host(x), B=3)) / np.linalg.norm(r)
     assert res < 1e-8
 
 
