@@ -16,13 +16,16 @@ struct CnnDims {
 
 // BF16 weights in the kernels' layouts (per layer 27 x 16 x 16) and biases.
 struct CnnPacked {
-  __nv_bfloat16* fwd;  // [3][27][co][ci]
-  __nv_bfloat16* bwd;  // [3][27][ci][co], taps flipped
-  float* bias;         // [3][16]
+  __nv_bfloat16* fwd;   // [3][27][co][ci]
+  __nv_bfloat16* bwd;   // [3][27][ci][co], taps flipped
+  float* bias;          // [3][16]
+  __nv_bfloat16* fwd1;  // first layer with K = (tap, channel): [4][co][16]
 };
 
 size_t cnn_partials_floats(const CnnDims& d);
 cudaError_t cnn_pack(const float* theta, CnnPacked& pk, cudaStream_t st);
+// ntiles: 2 (16 outputs), 1 (the last layer), or -1 for the first layer's
+// packed form (2 input channels, W = CnnPacked::fwd1)
 cudaError_t cnn_conv(const CnnDims& d, int epi, int ntiles, const __nv_bfloat16* in, const __nv_bfloat16* W,
                      const float* bias, const __nv_bfloat16* mask, void* out, cudaStream_t st);
 cudaError_t cnn_wgrad(const CnnDims& d, const __nv_bfloat16* in, const __nv_bfloat16* g, float* part, int layer,

@@ -11,6 +11,7 @@ size_t cnn_workspace_bytes(const CnnDims& d) {
   size_t b = 0;
   b += 2 * align256(3 * 27 * 256 * sizeof(__nv_bfloat16));  // packed weights, forward and transposed
   b += align256(48 * sizeof(float));                         // biases
+  b += align256(4 * 256 * sizeof(__nv_bfloat16));            // first layer, packed K
   b += 6 * align256(n * 16 * sizeof(__nv_bfloat16));         // a0, a1, a2, g1, g2, g3
   b += align256(n * sizeof(float));                          // y
   b += align256(cnn_partials_floats(d) * sizeof(float));     // weight-gradient partials
@@ -29,6 +30,7 @@ void cnn_carve(const CnnDims& d, void* base, CnnWork& w) {
   w.pk.fwd = (__nv_bfloat16*)take(3 * 27 * 256 * sizeof(__nv_bfloat16));
   w.pk.bwd = (__nv_bfloat16*)take(3 * 27 * 256 * sizeof(__nv_bfloat16));
   w.pk.bias = (float*)take(48 * sizeof(float));
+  w.pk.fwd1 = (__nv_bfloat16*)take(4 * 256 * sizeof(__nv_bfloat16));
   w.a0 = (__nv_bfloat16*)take(n * 32);
   w.a1 = (__nv_bfloat16*)take(n * 32);
   w.a2 = (__nv_bfloat16*)take(n * 32);
@@ -42,7 +44,7 @@ void cnn_carve(const CnnDims& d, void* base, CnnWork& w) {
 
 cudaError_t cnn_forward_packed(const CnnDims& d, CnnWork& w, cudaStream_t st) {
   const size_t L = 27 * 256;
-  cudaError_t e = cnn_conv(d, CNN_EPI_RELU, 2, w.a0, w.pk.fwd, w.pk.bias, nullptr, w.a1, st);
+  cudaError_t e = cnn_conv(d, CNN_EPI_RELU, -1, w.a0, w.pk.fwd1, w.pk.bias, nullptr, w.a1, st);
   if (e == cudaSuccess) e = cnn_conv(d, CNN_EPI_RELU, 2, w.a1, w.pk.fwd + L, w.pk.bias + 16, nullptr, w.a2, st);
   if (e == cudaSuccess) e = cnn_conv(d, CNN_EPI_OUT0_F32, 1, w.a2, w.pk.fwd + 2 * L, w.pk.bias + 32, nullptr, w.y, st);
   return e;

@@ -33,6 +33,25 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], unsigned a0, unsigned a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// Shared-memory rows of 16 BF16 channels (32 bytes) keep their two 16-byte
+// halves swapped on every other group of four rows.  A warp's fragment load
+// reads one 4-byte word from 8 consecutive rows; without the swap rows r and
+// r+4 fall on the same bank (2-way conflict), with it the 8 rows cover all
+// 32 banks.  smem_idx gives the element offset of channel c in row r.
+__device__ __forceinline__ int smem_idx(int r, int c) { return r * CH + ((((c >> 3) ^ (r >> 2)) & 1) << 3) + (c & 7); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const __nv_bfloat16* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+}
+__device__ __forceinline__ void ldsm_x2(unsigned (&r)[4], const __nv_bfloat16* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+  r[2] = r[3] = 0u;
+}
+
 struct Tile {
   int x0, y0, z0;
 };
@@ -60,7 +79,7 @@ __device__ __forceinline__ void load_brick(const CnnDims& d, const Tile& T, cons
       const long long p = ((long long)x * d.ny + y) * d.nz + z;
       val = reinterpret_cast<const uint4*>(in + p * CH)[half];
     }
-    reinterpret_cast<uint4*>(s_in + (size_t)v * CH)[half] = val;
+    reinterpret_cast<uint4*>(s_in + (size_t)v * CH)[half ^ ((v >> 2) & 1)] = val;
   }
 }
 
@@ -69,44 +88,87 @@ __device__ __forceinline__ void load_brick(const CnnDims& d, const Tile& T, cons
 // with the flipped, channel-transposed weights).  NT = number of 8-wide
 // output-channel tiles (2 for 16 outputs, 1 for the last layer).
 // ---------------------------------------------------------------------------
-template <int EPI, int NT>
+// Halo-brick row of the input voxel at tap t (0..26) of output row m0 of an
+// M tile (xl, yl, zhalf).
+__device__ __forceinline__ int tap_row(int t, int xl, int yl, int zh) {
+  const int dx = t / 9 - 1, dy = (t / 3) % 3 - 1, dz = t % 3 - 1;
+  return ((xl + dx + 1) * HY + (yl + dy + 1)) * HZ + zh * 16 + dz + 1;
+}
+
+// IN2: the input has 2 channels (the first layer).  Its K dimension is then
+// packed as 27 taps x 2 channels (padded to 64: four k-steps of 16) instead
+// of 27 taps x 16 channels, a seventh of the MMA work; Wt is [4][co 16][k 16]
+// with k = 2 * (tap - 8 * kstep) + ci.
+template <int EPI, int NT, bool IN2>
 __global__ void __launch_bounds__(NTHR) k_conv(CnnDims d, const __nv_bfloat16* __restrict__ in,
                                                const __nv_bfloat16* __restrict__ Wt,  // [27][co 16][ci 16]
                                                const float* __restrict__ bias,       // [16] or null
                                                const __nv_bfloat16* __restrict__ mask, void* out) {
+  constexpr int WROWS = IN2 ? 4 * CH : 27 * CH;  // weight rows of 16 elements
   __shared__ __align__(16) __nv_bfloat16 s_in[HX * HY * HZ * CH];
-  __shared__ __align__(16) __nv_bfloat16 s_w[27 * CH * CH];
+  __shared__ __align__(16) __nv_bfloat16 s_w[WROWS * CH];
   const Tile T = tile_of(d);
-  for (int q = threadIdx.x; q < 27 * CH * CH / 8; q += NTHR)
-    reinterpret_cast<uint4*>(s_w)[q] = reinterpret_cast<const uint4*>(Wt)[q];
+  for (int q = threadIdx.x; q < WROWS * CH / 8; q += NTHR)
+    reinterpret_cast<uint4*>(s_w)[q ^ (((q >> 3) & 1))] = reinterpret_cast<const uint4*>(Wt)[q];
   load_brick(d, T, in, s_in);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gid = lane >> 2, tig = lane & 3;
-  for (int mt = 0; mt < 2; ++mt) {
-    const int m = warp * 2 + mt;            // 0..15: (xl, yl, zhalf)
-    const int zh = m & 1, yl = (m >> 1) & 3, xl = m >> 3;
-    float acc[NT][4];
+  // the warp's two M tiles: 16 voxels along z each (z half mt) of column
+  // (xl, yl) of the brick
+  const int yl = warp & 3, xl = warp >> 2;
+  // ldmatrix addressing: lane l gives row (l & 7) of 8x8 matrix (l >> 3)
+  const int lr = lane & 7, lm = lane >> 3;
+  float acc[2][NT][4];
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll 3
-    for (int t = 0; t < 27; ++t) {
-      const int dx = t / 9 - 1, dy = (t / 3) % 3 - 1, dz = t % 3 - 1;
-      const int hbase = ((xl + dx + 1) * HY + (yl + dy + 1)) * HZ + zh * 16 + dz + 1;
-      const __nv_bfloat16* r0 = s_in + (size_t)(hbase + gid) * CH;
-      const __nv_bfloat16* r1 = s_in + (size_t)(hbase + gid + 8) * CH;
-      const unsigned a0 = *reinterpret_cast<const unsigned*>(r0 + tig * 2);
-      const unsigned a1 = *reinterpret_cast<const unsigned*>(r1 + tig * 2);
-      const unsigned a2 = *reinterpret_cast<const unsigned*>(r0 + tig * 2 + 8);
-      const unsigned a3 = *reinterpret_cast<const unsigned*>(r1 + tig * 2 + 8);
+  for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-      for (int nt = 0; nt < NT; ++nt) {
-        const __nv_bfloat16* wr = s_w + ((size_t)t * CH + nt * 8 + gid) * CH;
-        const unsigned b0 = *reinterpret_cast<const unsigned*>(wr + tig * 2);
-        const unsigned b1 = *reinterpret_cast<const unsigned*>(wr + tig * 2 + 8);
-        mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
+    for (int nt = 0; nt < NT; ++nt) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.f;
+  if (IN2) {
+    // k-step kk: this thread's columns k = 2*tig + {0,1} are tap 8kk + tig,
+    // columns k + 8 are tap 8kk + 4 + tig; channels 0 and 1 of each
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      unsigned b[4];
+      ldsm_x4(b, s_w + smem_idx(kk * CH + (lm >> 1) * 8 + lr, (lm & 1) * 8));
+      const int t0 = kk * 8 + tig, t1 = t0 + 4;
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        unsigned a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        if (t0 < 27) {
+          const int h = tap_row(t0, xl, yl, mt);
+          a0 = *reinterpret_cast<const unsigned*>(s_in + smem_idx(h + gid, 0));
+          a1 = *reinterpret_cast<const unsigned*>(s_in + smem_idx(h + gid + 8, 0));
+        }
+        if (t1 < 27) {
+          const int h = tap_row(t1, xl, yl, mt);
+          a2 = *reinterpret_cast<const unsigned*>(s_in + smem_idx(h + gid, 0));
+          a3 = *reinterpret_cast<const unsigned*>(s_in + smem_idx(h + gid + 8, 0));
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, b[2 * nt], b[2 * nt + 1]);
       }
     }
+  } else {
+#pragma unroll 3
+    for (int t = 0; t < 27; ++t) {
+      // B: (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15)
+      unsigned b[4];
+      if (NT == 2) ldsm_x4(b, s_w + smem_idx(t * CH + (lm >> 1) * 8 + lr, (lm & 1) * 8));
+      else ldsm_x2(b, s_w + smem_idx(t * CH + lr, (lm & 1) * 8));
+      const int hb = tap_row(t, xl, yl, 0);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        // A: (m 0-7, k 0-7), (m 8-15, k 0-7), (m 0-7, k 8-15), (m 8-15, k 8-15)
+        unsigned a[4];
+        ldsm_x4(a, s_in + smem_idx(hb + mt * 16 + lr + (lm & 1) * 8, (lm >> 1) * 8));
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a[0], a[1], a[2], a[3], b[2 * nt], b[2 * nt + 1]);
+      }
+    }
+  }
+  for (int mt = 0; mt < 2; ++mt) {
+    const int zh = mt;
     // epilogue: rows gid and gid+8 (voxels), columns tig*2, tig*2+1 (+8 nt)
     const int x = T.x0 + xl, y = T.y0 + yl;
 #pragma unroll
@@ -117,7 +179,7 @@ __global__ void __launch_bounds__(NTHR) k_conv(CnnDims d, const __nv_bfloat16* _
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) {
         const int co = nt * 8 + tig * 2;
-        float v0 = acc[nt][hr * 2], v1 = acc[nt][hr * 2 + 1];
+        float v0 = acc[mt][nt][hr * 2], v1 = acc[mt][nt][hr * 2 + 1];
         if (bias) {
           v0 += bias[co];
           v1 += bias[co + 1];
@@ -163,7 +225,7 @@ __global__ void __launch_bounds__(NTHR) k_conv_wgrad(CnnDims d, const __nv_bfloa
       const long long p = ((long long)x * d.ny + y) * d.nz + z;
       val = reinterpret_cast<const uint4*>(g + p * CH)[half];
     }
-    reinterpret_cast<uint4*>(s_g + (size_t)v * CH)[half] = val;
+    reinterpret_cast<uint4*>(s_g + (size_t)v * CH)[half ^ ((v >> 2) & 1)] = val;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -179,20 +241,16 @@ __global__ void __launch_bounds__(NTHR) k_conv_wgrad(CnnDims d, const __nv_bfloa
       const int hbase = ((xl + dx + 1) * HY + (yl + dy + 1)) * HZ + zh * 16 + dz + 1;
       const int k0 = tig * 2, k1 = tig * 2 + 1;
       // A[m = ci][k = voxel]
-      const unsigned a0 = pack2(s_in[(size_t)(hbase + k0) * CH + gid], s_in[(size_t)(hbase + k1) * CH + gid]);
-      const unsigned a1 =
-          pack2(s_in[(size_t)(hbase + k0) * CH + gid + 8], s_in[(size_t)(hbase + k1) * CH + gid + 8]);
-      const unsigned a2 =
-          pack2(s_in[(size_t)(hbase + k0 + 8) * CH + gid], s_in[(size_t)(hbase + k1 + 8) * CH + gid]);
-      const unsigned a3 =
-          pack2(s_in[(size_t)(hbase + k0 + 8) * CH + gid + 8], s_in[(size_t)(hbase + k1 + 8) * CH + gid + 8]);
+      const unsigned a0 = pack2(s_in[smem_idx(hbase + k0, gid)], s_in[smem_idx(hbase + k1, gid)]);
+      const unsigned a1 = pack2(s_in[smem_idx(hbase + k0, gid + 8)], s_in[smem_idx(hbase + k1, gid + 8)]);
+      const unsigned a2 = pack2(s_in[smem_idx(hbase + k0 + 8, gid)], s_in[smem_idx(hbase + k1 + 8, gid)]);
+      const unsigned a3 = pack2(s_in[smem_idx(hbase + k0 + 8, gid + 8)], s_in[smem_idx(hbase + k1 + 8, gid + 8)]);
 #pragma unroll
       for (int nt = 0; nt < 2; ++nt) {
         // B[k = voxel][n = co]
         const int co = nt * 8 + gid;
-        const unsigned b0 = pack2(s_g[(size_t)(gbase + k0) * CH + co], s_g[(size_t)(gbase + k1) * CH + co]);
-        const unsigned b1 =
-            pack2(s_g[(size_t)(gbase + k0 + 8) * CH + co], s_g[(size_t)(gbase + k1 + 8) * CH + co]);
+        const unsigned b0 = pack2(s_g[smem_idx(gbase + k0, co)], s_g[smem_idx(gbase + k1, co)]);
+        const unsigned b1 = pack2(s_g[smem_idx(gbase + k0 + 8, co)], s_g[smem_idx(gbase + k1 + 8, co)]);
         mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
       }
     }
@@ -208,7 +266,7 @@ __global__ void __launch_bounds__(NTHR) k_conv_wgrad(CnnDims d, const __nv_bfloa
   // bias gradient: column sums of g over the brick
   if (threadIdx.x < CH) {
     float s = 0.f;
-    for (int v = 0; v < TX * TY * TZ; ++v) s += __bfloat162float(s_g[(size_t)v * CH + threadIdx.x]);
+    for (int v = 0; v < TX * TY * TZ; ++v) s += __bfloat162float(s_g[smem_idx(v, threadIdx.x)]);
     out[27 * CH * CH + threadIdx.x] = s;
   }
 }
@@ -236,8 +294,14 @@ __global__ void k_reduce_grad(int nblocks, const float* __restrict__ part, int l
 //   bwd[l][t][ci][co] = W_l[co][ci][26 - t]     (flipped taps, channels swapped)
 // and FP32 biases padded to 16.
 __global__ void k_pack(const float* __restrict__ theta, __nv_bfloat16* __restrict__ fwd, __nv_bfloat16* __restrict__ bwd,
-                       float* __restrict__ bias) {
+                       float* __restrict__ bias, __nv_bfloat16* __restrict__ fwd1) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < 4 * CH * CH) {
+    // first layer, K packed as (tap, channel): fwd1[kk][co][k], tap = 8kk + k/2
+    const int kk = q / (CH * CH), co = (q / CH) % CH, k = q % CH;
+    const int tap = kk * 8 + k / 2, ci = k % 2;
+    fwd1[q] = __float2bfloat16(tap < 27 ? theta[cnn_woff(0) + (co * cnn_cin(0) + ci) * 27 + tap] : 0.f);
+  }
   if (q < 3 * CH) {
     const int l = q / CH, co = q % CH;
     bias[q] = co < cnn_cout(l) ? theta[cnn_woff(l) + cnn_cout(l) * cnn_cin(l) * 27 + co] : 0.f;
@@ -330,7 +394,7 @@ int conv_blocks(const CnnDims& d) {
 size_t cnn_partials_floats(const CnnDims& d) { return (size_t)conv_blocks(d) * (27 * CH * CH + CH); }
 
 cudaError_t cnn_pack(const float* theta, CnnPacked& pk, cudaStream_t st) {
-  k_pack<<<(3 * 27 * CH * CH + 255) / 256, 256, 0, st>>>(theta, pk.fwd, pk.bwd, pk.bias);
+  k_pack<<<(3 * 27 * CH * CH + 255) / 256, 256, 0, st>>>(theta, pk.fwd, pk.bwd, pk.bias, pk.fwd1);
   smg_count_launch(1);
   return cudaGetLastError();
 }
@@ -339,12 +403,13 @@ cudaError_t cnn_conv(const CnnDims& d, int epi, int ntiles, const __nv_bfloat16*
                      const float* bias, const __nv_bfloat16* mask, void* out, cudaStream_t st) {
   const int nb = conv_blocks(d);
   if (epi == CNN_EPI_OUT0_F32)
-    k_conv<CNN_EPI_OUT0_F32, 1><<<nb, NTHR, 0, st>>>(d, in, W, bias, mask, out);
+    k_conv<CNN_EPI_OUT0_F32, 1, false><<<nb, NTHR, 0, st>>>(d, in, W, bias, mask, out);
+  else if (epi == CNN_EPI_RELU && ntiles < 0)
+    k_conv<CNN_EPI_RELU, 2, true><<<nb, NTHR, 0, st>>>(d, in, W, bias, mask, out);
   else if (epi == CNN_EPI_RELU)
-    k_conv<CNN_EPI_RELU, 2><<<nb, NTHR, 0, st>>>(d, in, W, bias, mask, out);
+    k_conv<CNN_EPI_RELU, 2, false><<<nb, NTHR, 0, st>>>(d, in, W, bias, mask, out);
   else
-    k_conv<CNN_EPI_MASK, 2><<<nb, NTHR, 0, st>>>(d, in, W, bias, mask, out);
-  (void)ntiles;
+    k_conv<CNN_EPI_MASK, 2, false><<<nb, NTHR, 0, st>>>(d, in, W, bias, mask, out);
   smg_count_launch(1);
   return cudaGetLastError();
 }
