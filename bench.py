@@ -289,7 +289,7 @@ def run_ours(args, w, rank, world):
         vec = torch.empty(lvl0 * B, dtype=torch.float32, device=dev)
         rhs = b.float()
     ny = int(w["dims"][1])
-    kfile = "k_sweep3" if (B == 1 and ny <= 512) else ("k_sweep2" if B == 1 else "k_sweep (3x3 blocks)")
+    kfile = ("k_sweep3" if ny <= 512 else "k_sweep2") if B == 1 else ("k_bsweep3" if ny <= 512 else "k_sweep (3x3 blocks)")
     if w["smoother"] == 1:
         op, kname = smg.OP_ILU_LOWER, "%s (ILU(0) lower solve, level 0)" % kfile
         flops_pt, bytes_pt = 2 * nlow + 1, nlow * cbytes + 2 * vbytes + (4 if w["precision"] == 2 else 0)

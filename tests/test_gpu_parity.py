@@ -101,7 +101,8 @@ def test_spmv_and_residual(S, orc, d, off, B):
 
 @pytest.mark.parametrize("d,off", [((5, 6, 7), I.OFF27), ((9, 7, 11), I.OFF7), ((6, 9, 5), I.OFF19),
                                    ((1, 1, 13), I.OFF7), ((3, 1, 8), I.OFF27), ((8, 33, 6), I.OFF27),
-                                   ((6, 130, 9), I.OFF27), ((5, 97, 7), I.OFF7), ((4, 200, 3), I.OFF19)])
+                                   ((6, 130, 9), I.OFF27), ((5, 97, 7), I.OFF7), ((4, 200, 3), I.OFF19),
+                                   ((3, 530, 4), I.OFF27), ((2, 520, 3), I.OFF7)])
 def test_gs_sweeps_exact_order(S, orc, d, off):
     """Forward, backward and zero-guess sweeps reproduce the sequential
     lexicographic Gauss-Seidel (ragged grids, ny above one warp, 1-wide)."""
@@ -153,7 +154,9 @@ def test_block_gs_sweeps(S, orc, d):
     assert rel_max(host(u), orc.gs_backward(d, I.OFF7, A, Dinv, b, ref, B=3)) < TOL_KERNEL
 
 
-@pytest.mark.parametrize("d,off", [((8, 10, 12), I.OFF27), ((12, 8, 10), I.OFF7), ((8, 8, 9), I.OFF19)])
+# (3, 530, 4): planes wider than 16 warps use the plane-per-CTA kernels
+@pytest.mark.parametrize("d,off", [((8, 10, 12), I.OFF27), ((12, 8, 10), I.OFF7), ((8, 8, 9), I.OFF19),
+                                   ((3, 530, 4), I.OFF27), ((5, 70, 6), I.OFF27)])
 def test_ilu0_factor_and_apply(S, orc, d, off):
     A = rnd_sym27(d, 8, off)
     h = make(S, d, off, A, smoother=S.ILU0, max_levels=2)
