@@ -280,22 +280,28 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
 
           // (1) finish point K
           if (colok && K >= 0 && K < g.nz) {
+            // FOLD (FP64 / FP32): the partial sum of point k started from b and
+            // subtracted its terms, so accA = b - (partial sum): fewer FP64
+            // operations per point.  BF16 keeps b apart (the row scale
+            // multiplies the sum only).
+            constexpr bool FOLD = PK != KBF;
+            constexpr V sg = FOLD ? V(-1) : V(1);
             V sacc = accA;
 #pragma unroll
             for (int e = 0; e < NS; ++e) {
-              if (cls<NS, KIND, DIR>(e) == C_OWN) sacc = fma((V)to_c(cOwnA), carry, sacc);
+              if (cls<NS, KIND, DIR>(e) == C_OWN) sacc = fma(sg * (V)to_c(cOwnA), carry, sacc);
               if (cls<NS, KIND, DIR>(e) == C_LATE) {
                 const int kk = K + DIR * S::o(e, 2);
                 const V v = (J > 0 && kk >= 0 && kk < g.nz) ? hp[(kk & (kRing - 1)) * (NW * 32) + J - 1] : V(0);
-                sacc = fma((V)to_c(cLateA), v, sacc);
+                sacc = fma(sg * (V)to_c(cLateA), v, sacc);
               }
             }
             if (PK == KBF) sacc = (V)sA * sacc;
             V r;
             if (KIND == SW_ILU_L) {
-              r = bA - sacc;
+              r = FOLD ? sacc : bA - sacc;
             } else {
-              r = (bA - sacc) * dA;
+              r = (FOLD ? sacc : bA - sacc) * dA;
               if (KIND != SW_ILU_U && relax) r = (KIND == SW_GS_ZERO) ? wv * r : (V(1) - wv) * uoA + wv * r;
             }
             const int k = DIR > 0 ? K : g.nz - 1 - K;
@@ -311,7 +317,9 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
           // (2) partial sum of point K+1
           const int K1 = K + 1;
           if (colok && K1 >= 0 && K1 < g.nz) {
-            V a0 = V(0), a1 = V(0), a2 = V(0), a3 = V(0);
+            constexpr bool FOLD = PK != KBF;
+            constexpr V sg = FOLD ? V(-1) : V(1);
+            V a0 = FOLD ? bB : V(0), a1 = V(0), a2 = V(0), a3 = V(0);
             int q = 0;
 #pragma unroll
             for (int e = 0; e < NS; ++e) {
@@ -327,17 +335,15 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
                 has = true;
               }
               if (has) {
-                const V cv = (V)to_c(cB[e]);
-                if ((q & 3) == 0) a0 = fma(cv, tv, a0);
-                else if ((q & 3) == 1) a1 = fma(cv, tv, a1);
-                else if ((q & 3) == 2) a2 = fma(cv, tv, a2);
-                else a3 = fma(cv, tv, a3);
+                const V cv = sg * (V)to_c(cB[e]);
+                if ((q & 1) == 0) a0 = fma(cv, tv, a0);
+                else a1 = fma(cv, tv, a1);
                 ++q;
               }
               if (c == C_OWN) cOwnA = cB[e];
               if (c == C_LATE) cLateA = cB[e];
             }
-            accA = (a0 + a1) + (a2 + a3);
+            accA = a0 + a1;
             bA = bB;
             dA = dB;
             sA = sB;
