@@ -17,7 +17,7 @@ _lib = None
 
 ORC_OK, ORC_EINVAL, ORC_ENOMEM, ORC_EBREAKDOWN, ORC_ENOTCONV, ORC_ENAN = 0, 1, 2, 4, 5, 6
 SGS, ILU0 = 0, 1
-FW27V, PC8C = 0, 1
+FW27V, PC8C, C64C = 0, 1, 2
 FP64, FP32, BF16 = 0, 1, 2
 
 

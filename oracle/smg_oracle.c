@@ -284,13 +284,25 @@ void orc_ilu0_apply(const int d[3], int ns, const int* off, const double* LU, co
 }
 
 /* ------------------------------------------------------------------------- */
-/* Grid transfers (Sec. 2 V-cycle; Table 3 patterns 3d27v and 3d8c)          */
+/* Grid transfers (Sec. 2 V-cycle; Table 3 patterns 3d27v, 3d8c and 3d64c)  */
 /* ------------------------------------------------------------------------- */
 /* Transfer 0 = vertex full weighting: coarse point I sits on fine point 2I+1;
  *   P(v,J) = prod_d w(v_d - (2J_d+1)), w(0)=1, w(+-1)=1/2 (trilinear, 3d27v),
  *   R = P^T / 8 (full weighting).
  * Transfer 1 = cell piecewise constant 3d8c: R(I,u) = 1 for u in 2I+{0,1}^3,
- *   P = R^T. */
+ *   P = R^T.
+ * Transfer 2 = cell-centred trilinear interpolation 3d64c with the 3d8c
+ *   restriction of transfer 1 (Table 3 columns 3d8c / A / 3d64c; the
+ *   interpolation of the Table 8 settings for rhd-3T and solid-3D).  Coarse
+ *   cell J covers fine cells 2J and 2J+1 in every dimension; a fine cell
+ *   centre lies a quarter of a coarse cell from the centre of its own coarse
+ *   cell and three quarters from the nearest other one, so per dimension
+ *   c(v - 2J) = 3/4 for v - 2J in {0, 1} and 1/4 for v - 2J in {-1, 2}, and
+ *   P(v,J) = prod_d c(v_d - 2J_d): every coarse cell feeds the 4^3 = 64 fine
+ *   cells 2J + {-1,0,1,2}^3 (hence "3d64c"), every fine cell takes 8 coarse
+ *   cells.  Coarse cells off the grid are dropped (their weight is lost, as
+ *   for the vertex transfer).  R is not a multiple of P^T, so A^C is in
+ *   general nonsymmetric. */
 
 void orc_coarse_dims(const int f[3], int c[3]) {
   for (int t = 0; t < 3; ++t) c[t] = f[t] / 2;
@@ -298,9 +310,13 @@ void orc_coarse_dims(const int f[3], int c[3]) {
 
 static double w1(int dlt) { return dlt == 0 ? 1.0 : (dlt == 1 || dlt == -1 ? 0.5 : 0.0); }
 
+/* 1-D cell-centred linear interpolation weight of fine cell 2J + d from coarse cell J */
+static double wc(int d) { return (d == 0 || d == 1) ? 0.75 : ((d == -1 || d == 2) ? 0.25 : 0.0); }
+
 /* P(v,J) for fine point v, coarse point J */
 static double pweight(int transfer, const int* v, const int* J) {
   if (transfer == 0) return w1(v[0] - (2 * J[0] + 1)) * w1(v[1] - (2 * J[1] + 1)) * w1(v[2] - (2 * J[2] + 1));
+  if (transfer == 2) return wc(v[0] - 2 * J[0]) * wc(v[1] - 2 * J[1]) * wc(v[2] - 2 * J[2]);
   for (int t = 0; t < 3; ++t)
     if (v[t] - 2 * J[t] < 0 || v[t] - 2 * J[t] > 1) return 0.0;
   return 1.0;
@@ -308,7 +324,7 @@ static double pweight(int transfer, const int* v, const int* J) {
 
 /* R(I,u) */
 static double rweight(int transfer, const int* I, const int* u) {
-  return transfer == 0 ? pweight(0, u, I) / 8.0 : pweight(1, u, I);
+  return transfer == 0 ? pweight(0, u, I) / 8.0 : pweight(1, u, I); /* transfers 1 and 2: 3d8c */
 }
 
 /* fine points that the coarse point I touches: base + [0, span)^3 */
@@ -620,6 +636,7 @@ int orc_mg_setup(void** out, const int d[3], int ns, const int* off, int B, cons
   *out = NULL;
   if (orc_mask_validate(ns, off)) return ORC_EINVAL;
   if (B != 1 && B != 3) return ORC_EINVAL;
+  if (transfer < 0 || transfer > 2) return ORC_EINVAL;
   if (B == 3 && smoother != SM_SGS) return ORC_EINVAL;
   if (precision != 0 && B != 1) return ORC_EINVAL;
   for (int t = 0; t < 3; ++t)
