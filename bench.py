@@ -58,6 +58,16 @@ WORKLOADS = {
                                                                           batch=4, lr=1e-3)),
     "c5_plain": dict(desc="varcoef7_256^3_sgs_fw27v_pcg_fp64", dims=(256, 256, 256), gen="fv", smoother=0,
                      transfer=0, precision=0, krylov=0, tol=1e-9),
+    # the same cell-centred variable-coefficient 7-point matrix with ILU(0) and
+    # the cell-centred transfer pair (3d64c interpolation, 3d8c restriction:
+    # Table 8's rhd-3T setting), whose V-cycle is nonsymmetric -> FPCG / FGMRES;
+    # c6_fw27v is the vertex pair on the same problem for comparison
+    "c6": dict(desc="varcoef7_256^3_ilu0_c64c_fpcg_fp64", dims=(256, 256, 256), gen="fv", smoother=1, transfer=2,
+               precision=0, krylov=1, tol=1e-9),
+    "c6_fgmres": dict(desc="varcoef7_256^3_ilu0_c64c_fgmres30_fp64", dims=(256, 256, 256), gen="fv", smoother=1,
+                      transfer=2, precision=0, krylov=2, tol=1e-9),
+    "c6_fw27v": dict(desc="varcoef7_256^3_ilu0_fw27v_fpcg_fp64", dims=(256, 256, 256), gen="fv", smoother=1,
+                     transfer=0, precision=0, krylov=1, tol=1e-9),
 }
 DEFAULT = "c2"
 HBM_PEAK_FALLBACK = 6800.0
@@ -428,7 +438,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     metric = "time to solution (set-up + Krylov to rel-res %g), %s" % (w["tol"], w["desc"])
     config = {"workload": w["desc"], "dims": list(w["dims"]), "unknowns_per_point": w.get("block", 1),
-              "smoother": ["sym-GS", "ILU(0)"][w["smoother"]], "transfer": ["3d27v", "3d8c"][w["transfer"]],
+              "smoother": ["sym-GS", "ILU(0)"][w["smoother"]], "transfer": ["3d27v", "3d8c", "3d64c interp. + 3d8c restr."][w["transfer"]],
               "hierarchy_precision": ["fp64", "fp32", "bf16-rowscaled"][w["precision"]],
               "krylov": ["PCG", "FPCG", "FGMRES(30)"][w["krylov"]], "tol": w["tol"],
               "parallelism": "replicas" if args.gpus > 1 else "single-gpu",

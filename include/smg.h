@@ -49,7 +49,7 @@ typedef enum {
 } smg_status;
 
 enum { SMG_SMOOTHER_SGS = 0, SMG_SMOOTHER_ILU0 = 1 };
-enum { SMG_TRANSFER_FW27V = 0, SMG_TRANSFER_PC8C = 1 };
+enum { SMG_TRANSFER_FW27V = 0, SMG_TRANSFER_PC8C = 1, SMG_TRANSFER_C64C = 2 };
 enum { SMG_PREC_FP64 = 0, SMG_PREC_FP32 = 1, SMG_PREC_BF16 = 2 };
 enum { SMG_KRYLOV_PCG = 0, SMG_KRYLOV_FPCG = 1, SMG_KRYLOV_FGMRES = 2 };
 
@@ -62,7 +62,15 @@ enum { SMG_KRYLOV_PCG = 0, SMG_KRYLOV_FPCG = 1, SMG_KRYLOV_FGMRES = 2 };
  *  transfer   [FW27V] vertex full weighting: coarse I on fine 2I+1, trilinear
  *                    P and R = P^T/8 (Table 3 pattern 3d27v); PC8C: cell
  *                    piecewise constant, R(I,u)=1 on u in 2I+{0,1}^3, P = R^T
- *                    (Table 3 pattern 3d8c).
+ *                    (Table 3 pattern 3d8c); C64C: the same 3d8c restriction
+ *                    with cell-centred trilinear interpolation, per dimension
+ *                    3/4 from the fine cell's own coarse cell and 1/4 from
+ *                    the next one on its side, coarse cells off the grid
+ *                    dropped (Table 3 columns 3d8c / A / 3d64c; the Table 8
+ *                    settings of rhd-3T and solid-3D).  R is not a multiple
+ *                    of P^T, so the coarse operators and the V-cycle are
+ *                    nonsymmetric: use FPCG or FGMRES (PCG is accepted; the
+ *                    paper runs CG with it).
  *  precision  [FP64] storage and arithmetic of the hierarchy and V-cycle:
  *                    FP64, FP32, or BF16 values with one FP32 scale per row
  *                    and FP32 accumulation (not in the paper).  The Krylov

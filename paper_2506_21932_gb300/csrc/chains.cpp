@@ -44,18 +44,32 @@ int derive_chains(int dim, int nr, const int* roff, int na, const int* aoff, int
 // 1-D full-weighting interpolation weight of fine offset d from the anchor.
 static double w1(int d) { return d == 0 ? 1.0 : 0.5; }
 
+// 1-D cell-centred interpolation weight of fine cell 2J + d from coarse cell J
+// (3d64c): the fine centre is 1/4 of a coarse cell from J's centre for d in
+// {0,1} and 3/4 from it for d in {-1,2}.
+static double wc(int d) { return (d == 0 || d == 1) ? 0.75 : 0.25; }
+
+// The fine offsets lo..hi in every dimension, lexicographic.
+static void cube(int lo, int hi, std::vector<int>& out) {
+  for (int a = lo; a <= hi; ++a)
+    for (int b = lo; b <= hi; ++b)
+      for (int c = lo; c <= hi; ++c) out.insert(out.end(), {a, b, c});
+}
+
 int build_rap_table(int transfer, int ns_f, const int (*off_f)[3], RapTable& T) {
   std::vector<int> rp, pp;  // R and P patterns: fine offsets from the anchor
   if (transfer == SMG_TRANSFER_FW27V) {
-    for (int a = -1; a <= 1; ++a)
-      for (int b = -1; b <= 1; ++b)
-        for (int c = -1; c <= 1; ++c) { rp.insert(rp.end(), {a, b, c}); }
+    cube(-1, 1, rp);  // anchor 2I+1
+    pp = rp;
+  } else if (transfer == SMG_TRANSFER_PC8C) {
+    cube(0, 1, rp);  // anchor 2I
+    pp = rp;
+  } else if (transfer == SMG_TRANSFER_C64C) {
+    cube(0, 1, rp);
+    cube(-1, 2, pp);
   } else {
-    for (int a = 0; a <= 1; ++a)
-      for (int b = 0; b <= 1; ++b)
-        for (int c = 0; c <= 1; ++c) { rp.insert(rp.end(), {a, b, c}); }
+    return -1;
   }
-  pp = rp;
   std::vector<int> af(3 * ns_f);
   for (int e = 0; e < ns_f; ++e)
     for (int t = 0; t < 3; ++t) af[3 * e + t] = off_f[e][t];
@@ -89,6 +103,8 @@ int build_rap_table(int transfer, int ns_f, const int (*off_f)[3], RapTable& T) 
       if (transfer == SMG_TRANSFER_FW27V) {
         wr = w1(ro[0]) * w1(ro[1]) * w1(ro[2]) / 8.0;
         wp = w1(po[0]) * w1(po[1]) * w1(po[2]);
+      } else if (transfer == SMG_TRANSFER_C64C) {
+        wp = wc(po[0]) * wc(po[1]) * wc(po[2]);
       }
       RapEntry en;
       en.rx = ro[0]; en.ry = ro[1]; en.rz = ro[2];

@@ -1,5 +1,5 @@
 // Point-parallel stencil kernels: SG-DIA SpMV / residual (Sec. 6.1.1), grid
-// transfers (Sec. 2 V-cycle; Table 3 patterns 3d27v and 3d8c), precision
+// transfers (Sec. 2 V-cycle; Table 3 patterns 3d27v, 3d8c and 3d64c), precision
 // casts and lowering, diagonal inverses and the dense coarsest level.
 #include "smg_internal.cuh"
 
@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(TPB) k_spmv3(Grid g, Stencil s, const V* __res
 // ---------------------------------------------------------------------------
 // Transfers.  Full weighting (3d27v): coarse I sits on fine 2I+1, 1-D weights
 // (1/2, 1, 1/2); R = P^T/8.  Piecewise constant (3d8c): R(I,u) = 1 on
-// u in 2I+{0,1}^3, P = R^T.  Fine points off the grid are skipped.
+// u in 2I+{0,1}^3, P = R^T.  Cell-centred trilinear (3d64c): the 3d8c
+// restriction with the interpolation of k_prolong_c64.  Fine points off the
+// grid are skipped.
 // ---------------------------------------------------------------------------
 template <typename V, int B>
 __global__ void __launch_bounds__(TPB) k_restrict_fw(Grid f, Grid c, const V* __restrict__ rf, V* __restrict__ fc) {
@@ -197,6 +199,55 @@ __global__ void __launch_bounds__(TPB) k_prolong_fw(Grid f, Grid c, const V* __r
         if (cc >= cnt[2] || (unsigned)J2 >= (unsigned)cn[2]) continue;
         V wgt = w[0][a] * w[1][b] * w[2][cc];
         long long P = ((long long)J0 * c.ny + J1) * c.nz + J2;
+#pragma unroll
+        for (int r = 0; r < B; ++r) acc[r] = fma(wgt, ec[P * B + r], acc[r]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < B; ++r) uf[q * B + r] += acc[r];
+}
+
+// uf += P ec for the cell-centred trilinear interpolation (3d64c).  Per
+// dimension, fine cell v lies in coarse cell v/2 (weight 3/4) and takes 1/4
+// from the coarse cell on its side: v/2 - 1 for even v, v/2 + 1 for odd v.
+// Coarse cells off the grid are dropped.  The pair (lower, upper) of coarse
+// cells is summed in increasing order in every dimension.
+template <typename V, int B>
+__global__ void __launch_bounds__(TPB) k_prolong_c64(Grid f, Grid c, const V* __restrict__ ec, V* __restrict__ uf) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= f.n) return;
+  int v0, v1, v2;
+  coords(q, f, v0, v1, v2);
+  const int v[3] = {v0, v1, v2};
+  const int cn[3] = {c.nx, c.ny, c.nz};
+  int lo[3];
+  V w[3][2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (v[d] & 1) {
+      lo[d] = v[d] >> 1; w[d][0] = V(0.75); w[d][1] = V(0.25);
+    } else {
+      lo[d] = (v[d] >> 1) - 1; w[d][0] = V(0.25); w[d][1] = V(0.75);
+    }
+  }
+  V acc[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) acc[r] = 0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int J0 = lo[0] + a;
+    if ((unsigned)J0 >= (unsigned)cn[0]) continue;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int J1 = lo[1] + b;
+      if ((unsigned)J1 >= (unsigned)cn[1]) continue;
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        const int J2 = lo[2] + cc;
+        if ((unsigned)J2 >= (unsigned)cn[2]) continue;
+        const V wgt = w[0][a] * w[1][b] * w[2][cc];
+        const long long P = ((long long)J0 * c.ny + J1) * c.nz + J2;
 #pragma unroll
         for (int r = 0; r < B; ++r) acc[r] = fma(wgt, ec[P * B + r], acc[r]);
       }
@@ -503,6 +554,8 @@ cudaError_t launch_prolong_add(int transfer, Grid f, int B, int pk, const void* 
 #define PCASE(V, BB)                                                                                   \
   if (transfer == SMG_TRANSFER_FW27V)                                                                  \
     k_prolong_fw<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)ec, (V*)uf);                               \
+  else if (transfer == SMG_TRANSFER_C64C)                                                              \
+    k_prolong_c64<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)ec, (V*)uf);                              \
   else                                                                                                 \
     k_prolong_pc<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)ec, (V*)uf);
   if (dbl) {

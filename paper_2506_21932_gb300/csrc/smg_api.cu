@@ -629,7 +629,7 @@ extern "C" int smg_setup(smg_t* out, const int dims[3], int nstencil, const int*
   TRY(validate_mask(nstencil, offsets));
   smg_options o{};
   if (opt) o = *opt;
-  if (o.smoother < 0 || o.smoother > 1 || o.transfer < 0 || o.transfer > 1 || o.precision < 0 || o.precision > 2 ||
+  if (o.smoother < 0 || o.smoother > 1 || o.transfer < 0 || o.transfer > 2 || o.precision < 0 || o.precision > 2 ||
       o.krylov < 0 || o.krylov > 2)
     return SMG_EINVAL;
   if (o.restart == 0) o.restart = 30;

@@ -194,10 +194,13 @@ def test_ilu0_tridiagonal_exact_solve(S, orc):
 
 @pytest.mark.parametrize("d,off,transfer,B,gen", [
     ((16, 12, 20), I.OFF7, 0, 1, "lap"), ((16, 16, 16), I.OFF27, 0, 1, "q1"), ((24, 16, 16), I.OFF27, 0, 1, "rnd"),
-    ((16, 16, 8), I.OFF7, 1, 3, "blk"), ((16, 8, 24), I.OFF7, 1, 1, "rnd")])
+    ((16, 16, 8), I.OFF7, 1, 3, "blk"), ((16, 8, 24), I.OFF7, 1, 1, "rnd"),
+    ((16, 12, 20), I.OFF7, 2, 1, "lap"), ((16, 16, 16), I.OFF27, 2, 1, "q1"), ((24, 16, 16), I.OFF19, 2, 1, "rnd"),
+    ((16, 16, 8), I.OFF7, 2, 3, "blk"), ((16, 8, 24), I.OFF7, 2, 1, "fv")])
 def test_galerkin_hierarchy(S, orc, d, off, transfer, B, gen):
     A = {"lap": lambda: I.laplace7(d).numpy(), "q1": lambda: I.q1_aniso27(d, 2).numpy(),
-         "rnd": lambda: rnd_sym27(d, 5, off), "blk": lambda: I.block7_layered(d, 4).numpy()}[gen]()
+         "rnd": lambda: rnd_sym27(d, 5, off), "blk": lambda: I.block7_layered(d, 4).numpy(),
+         "fv": lambda: I.varcoef7(d, 4)[0].numpy()}[gen]()
     h = make(S, d, off, A, block=B, transfer=transfer, smoother=S.SGS)
     ref = orc.MG(d, off, A, B=B, smoother=orc.SGS, transfer=transfer)
     assert h.nlevels == ref.nlevels
@@ -219,7 +222,7 @@ def test_galerkin_hierarchy(S, orc, d, off, transfer, B, gen):
         assert np.all(Ag.reshape(pad.shape)[pad] == 0.0)
 
 
-@pytest.mark.parametrize("transfer,B", [(0, 1), (1, 1), (0, 3), (1, 3)])
+@pytest.mark.parametrize("transfer,B", [(0, 1), (1, 1), (2, 1), (0, 3), (1, 3), (2, 3)])
 def test_restrict_prolong(S, orc, transfer, B):
     d = (10, 12, 8) if B == 1 else (8, 8, 10)
     A = I.laplace7(d).numpy() if B == 1 else I.block7_layered(d, 0).numpy()
@@ -241,7 +244,8 @@ def test_restrict_prolong(S, orc, transfer, B):
 # ---------------------------------------------------------------------------
 
 VCASES = [((32, 32, 32), "lap", 0, 0, 1), ((24, 16, 32), "q1", 1, 0, 1), ((16, 24, 16), "q1", 0, 0, 1),
-          ((16, 16, 16), "blk", 0, 1, 3), ((20, 16, 24), "q1", 1, 0, 1)]
+          ((16, 16, 16), "blk", 0, 1, 3), ((20, 16, 24), "q1", 1, 0, 1), ((32, 32, 32), "fv", 0, 2, 1),
+          ((24, 16, 32), "fv", 1, 2, 1), ((16, 24, 16), "q1", 1, 2, 1), ((16, 16, 16), "blk", 0, 2, 3)]
 
 
 def problem(kind, d, seed=1):
@@ -292,6 +296,28 @@ def test_pcg_solve_matches_oracle(S, orc, d, kind, smoother, krylov):
     # the true residual, recomputed by the oracle from the GPU solution
     res = np.linalg.norm(orc.residual(d, off, A, b, host(x))) / np.linalg.norm(b)
     assert res < 1e-9 and abs(res - rr) < 1e-12
+
+
+@pytest.mark.parametrize("kind,smoother,krylov", [("fv", 0, 1), ("fv", 1, 2), ("lap", 1, 1), ("q1", 1, 2)])
+def test_cell64_solves_match_oracle(S, orc, kind, smoother, krylov):
+    """Cell-centred 3d64c interpolation with 3d8c restriction (nonsymmetric
+    V-cycle) under flexible PCG and FGMRES(30): same iteration count as the
+    oracle within one, tolerance reached, true residual recomputed by the
+    oracle."""
+    d = (32, 24, 32)
+    off, A = problem(kind, d)
+    b = I.rhs(np.prod(d), 2).numpy()
+    h = make(S, d, off, A, smoother=smoother, transfer=S.C64C, krylov=krylov, restart=30)
+    x = torch.zeros_like(cu(b))
+    it, rr, rc = h.solve(cu(b), x, tol=1e-9, maxit=300)
+    ref = orc.MG(d, off, A, smoother=smoother, transfer=orc.C64C)
+    if krylov == 2:
+        _, rcr, itr, _, _ = ref.fgmres(b, tol=1e-9, restart=30, maxit=300)
+    else:
+        _, rcr, itr, _, _ = ref.pcg(b, tol=1e-9, flexible=True, maxit=300)
+    assert rc == 0 and rcr == 0 and abs(it - itr) <= 1 and rr < 1e-9
+    res = np.linalg.norm(orc.residual(d, off, A, b, host(x))) / np.linalg.norm(b)
+    assert res < 1e-9
 
 
 def test_fgmres_block_solve_matches_oracle(S, orc):
