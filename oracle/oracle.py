@@ -16,7 +16,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 ORC_OK, ORC_EINVAL, ORC_ENOMEM, ORC_EBREAKDOWN, ORC_ENOTCONV, ORC_ENAN = 0, 1, 2, 4, 5, 6
-SGS, ILU0 = 0, 1
+SGS, ILU0, LGS = 0, 1, 2
 FW27V, PC8C, C64C = 0, 1, 2
 FP64, FP32, BF16 = 0, 1, 2
 
@@ -103,6 +103,25 @@ def gs_backward(d, off, A, Dinv, b, u, w=1.0, B=1):
     u = _f64(u).copy()
     lib().orc_gs_backward(_p(d), len(o), _p(o), B, _p(A), _p(Dinv), _p(b), _p(u), ctypes.c_double(w))
     return u
+
+
+def lgs_forward(d, off, A, b, u):
+    d, o, A, b = _i3(d), _offs(off), _f64(A), _f64(b)
+    u = _f64(u).copy()
+    lib().orc_lgs_forward(_p(d), len(o), _p(o), _p(A), _p(b), _p(u))
+    return u
+
+
+def lgs_backward(d, off, A, b, u):
+    d, o, A, b = _i3(d), _offs(off), _f64(A), _f64(b)
+    u = _f64(u).copy()
+    lib().orc_lgs_backward(_p(d), len(o), _p(o), _p(A), _p(b), _p(u))
+    return u
+
+
+def lgs_check(d, off, A, spd_check=True):
+    d, o, A = _i3(d), _offs(off), _f64(A)
+    return lib().orc_lgs_check(_p(d), len(o), _p(o), _p(A), int(spd_check))
 
 
 def ilu0_factor(d, off, A, spd_check=True):

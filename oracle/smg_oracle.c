@@ -197,6 +197,89 @@ void orc_gs_backward(const int d[3], int ns, const int* off, int B, const double
 }
 
 /* ------------------------------------------------------------------------- */
+/* Line Gauss-Seidel along z (Sec. 4.4, LGS): the points of a z-column       */
+/* (i, j) are updated together.  The right-hand side of the column gathers   */
+/* b minus every coupling to another column (columns earlier in the sweep   */
+/* already hold new values), and the tridiagonal system formed by the        */
+/* offsets (0,0,-1), (0,0,0), (0,0,+1) is solved by the Thomas algorithm.    */
+/* Scalar problems only; the relaxation weight is 1.                         */
+/* ------------------------------------------------------------------------- */
+
+/* stencil entries of the column's tridiagonal part (-1 where absent) */
+static void line_entries(int ns, const int* off, int* esub, int* ediag, int* esup) {
+  *esub = find_off(ns, off, 0, 0, -1);
+  *ediag = find_off(ns, off, 0, 0, 0);
+  *esup = find_off(ns, off, 0, 0, 1);
+}
+
+/* Thomas elimination pivots of every column; ORC_EBREAKDOWN if one is zero,
+ * or not positive when spd_check is set. */
+int orc_lgs_check(const int d[3], int ns, const int* off, const double* A, int spd_check) {
+  int es, ed, eu;
+  line_entries(ns, off, &es, &ed, &eu);
+  if (ed < 0) return ORC_EBREAKDOWN;
+  for (int i = 0; i < d[0]; ++i)
+    for (int j = 0; j < d[1]; ++j) {
+      double cprev = 0.0;
+      for (int k = 0; k < d[2]; ++k) {
+        long p = pidx(d, i, j, k);
+        double sub = (es >= 0 && k > 0) ? A[p * ns + es] : 0.0;
+        double sup = (eu >= 0 && k + 1 < d[2]) ? A[p * ns + eu] : 0.0;
+        double m = A[p * ns + ed] - sub * cprev;
+        if (m == 0.0 || (spd_check && !(m > 0.0))) return ORC_EBREAKDOWN;
+        cprev = sup / m;
+      }
+    }
+  return ORC_OK;
+}
+
+/* Update column (i, j) in place.  rhs, cp, dp: scratch of d[2] doubles. */
+static void lgs_column(const int d[3], int ns, const int* off, const double* A, const double* b, double* u, int i,
+                       int j, double* rhs, double* cp, double* dp) {
+  int es, ed, eu;
+  line_entries(ns, off, &es, &ed, &eu);
+  int nz = d[2];
+  for (int k = 0; k < nz; ++k) {
+    long p = pidx(d, i, j, k);
+    double s = b[p];
+    for (int e = 0; e < ns; ++e) {
+      if (off[3 * e] == 0 && off[3 * e + 1] == 0) continue; /* in the column */
+      int a = i + off[3 * e], bb = j + off[3 * e + 1], c = k + off[3 * e + 2];
+      if (!inside(d, a, bb, c)) continue;
+      s -= A[p * ns + e] * u[pidx(d, a, bb, c)];
+    }
+    rhs[k] = s;
+  }
+  /* Thomas: forward elimination, then back substitution */
+  for (int k = 0; k < nz; ++k) {
+    long p = pidx(d, i, j, k);
+    double sub = (es >= 0 && k > 0) ? A[p * ns + es] : 0.0;
+    double sup = (eu >= 0 && k + 1 < nz) ? A[p * ns + eu] : 0.0;
+    double m = A[p * ns + ed] - (k > 0 ? sub * cp[k - 1] : 0.0);
+    cp[k] = sup / m;
+    dp[k] = (rhs[k] - (k > 0 ? sub * dp[k - 1] : 0.0)) / m;
+  }
+  u[pidx(d, i, j, nz - 1)] = dp[nz - 1];
+  for (int k = nz - 2; k >= 0; --k) u[pidx(d, i, j, k)] = dp[k] - cp[k] * u[pidx(d, i, j, k + 1)];
+}
+
+/* Forward line sweep: columns in lexicographic (i, j) order. */
+void orc_lgs_forward(const int d[3], int ns, const int* off, const double* A, const double* b, double* u) {
+  double* t = (double*)malloc(sizeof(double) * 3 * d[2]);
+  for (int i = 0; i < d[0]; ++i)
+    for (int j = 0; j < d[1]; ++j) lgs_column(d, ns, off, A, b, u, i, j, t, t + d[2], t + 2 * d[2]);
+  free(t);
+}
+
+/* Backward line sweep: the same column update in the reverse column order. */
+void orc_lgs_backward(const int d[3], int ns, const int* off, const double* A, const double* b, double* u) {
+  double* t = (double*)malloc(sizeof(double) * 3 * d[2]);
+  for (int i = d[0] - 1; i >= 0; --i)
+    for (int j = d[1] - 1; j >= 0; --j) lgs_column(d, ns, off, A, b, u, i, j, t, t + d[2], t + 2 * d[2]);
+  free(t);
+}
+
+/* ------------------------------------------------------------------------- */
 /* ILU(0) on the matrix mask (Sec. 4.2 "Flexibility" and Sec. 4.4 ILU formula) */
 /* ------------------------------------------------------------------------- */
 
@@ -576,7 +659,7 @@ void orc_lower_matrix(const int d[3], int ns, const int* off, const double* A, i
 /* Multigrid hierarchy and V-cycle (Sec. 2, Fig. 1 V-cycle; Eq. 1 T_tot)     */
 /* ------------------------------------------------------------------------- */
 
-enum { SM_SGS = 0, SM_ILU0 = 1 };
+enum { SM_SGS = 0, SM_ILU0 = 1, SM_LGS = 2 };
 
 typedef struct {
   int d[3], ns, off[27 * 3];
@@ -638,6 +721,8 @@ int orc_mg_setup(void** out, const int d[3], int ns, const int* off, int B, cons
   if (B != 1 && B != 3) return ORC_EINVAL;
   if (transfer < 0 || transfer > 2) return ORC_EINVAL;
   if (B == 3 && smoother != SM_SGS) return ORC_EINVAL;
+  if (smoother < SM_SGS || smoother > SM_LGS) return ORC_EINVAL;
+  if (smoother == SM_LGS && (precision != 0 || w != 1.0)) return ORC_EINVAL;
   if (precision != 0 && B != 1) return ORC_EINVAL;
   for (int t = 0; t < 3; ++t)
     if (d[t] < 1) return ORC_EINVAL;
@@ -683,6 +768,8 @@ int orc_mg_setup(void** out, const int d[3], int ns, const int* off, int B, cons
       if (smoother == SM_SGS) {
         L->Dinv = (double*)malloc(sizeof(double) * n * B * B);
         rc = orc_diag_inverse(L->d, L->ns, L->off, B, L->A, L->Dinv);
+      } else if (smoother == SM_LGS) {
+        rc = orc_lgs_check(L->d, L->ns, L->off, L->A, 1);
       } else {
         L->LU = (double*)malloc(sizeof(double) * n * L->ns);
         L->Udinv = (double*)malloc(sizeof(double) * n);
@@ -768,6 +855,9 @@ static void smooth_pre64(orc_mg* mg, orc_level* L, const double* f, double* u) {
   if (mg->smoother == SM_SGS) {
     orc_gs_forward(L->d, L->ns, L->off, mg->B, L->A, L->Dinv, f, u, mg->w);
     orc_gs_backward(L->d, L->ns, L->off, mg->B, L->A, L->Dinv, f, u, mg->w);
+  } else if (mg->smoother == SM_LGS) {
+    orc_lgs_forward(L->d, L->ns, L->off, L->A, f, u);
+    orc_lgs_backward(L->d, L->ns, L->off, L->A, f, u);
   } else {
     orc_ilu0_apply(L->d, L->ns, L->off, L->LU, L->Udinv, f, u);
   }
@@ -778,6 +868,9 @@ static void smooth_post64(orc_mg* mg, orc_level* L, const double* f, double* u) 
   if (mg->smoother == SM_SGS) {
     orc_gs_forward(L->d, L->ns, L->off, mg->B, L->A, L->Dinv, f, u, mg->w);
     orc_gs_backward(L->d, L->ns, L->off, mg->B, L->A, L->Dinv, f, u, mg->w);
+  } else if (mg->smoother == SM_LGS) {
+    orc_lgs_forward(L->d, L->ns, L->off, L->A, f, u);
+    orc_lgs_backward(L->d, L->ns, L->off, L->A, f, u);
   } else {
     long n = npts(L->d);
     double* r = (double*)malloc(sizeof(double) * n);
