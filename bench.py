@@ -68,6 +68,12 @@ WORKLOADS = {
                       transfer=2, precision=0, krylov=2, tol=1e-9),
     "c6_fw27v": dict(desc="varcoef7_256^3_ilu0_fw27v_fpcg_fp64", dims=(256, 256, 256), gen="fv", smoother=1,
                      transfer=0, precision=0, krylov=1, tol=1e-9),
+    # 27-point Q1 diffusion with the strong coupling along z (k = 1e-3, 1e-3,
+    # 1): symmetric line Gauss-Seidel along z (Sec. 4.4 LGS), PCG
+    "c7": dict(desc="zaniso27_256^3_lgs_fw27v_pcg_fp64", dims=(256, 256, 256), gen="q1z", smoother=2, transfer=0,
+               precision=0, krylov=0, tol=1e-9),
+    "c7_128": dict(desc="zaniso27_128^3_lgs_fw27v_pcg_fp64", dims=(128, 128, 128), gen="q1z", smoother=2,
+                   transfer=0, precision=0, krylov=0, tol=1e-9),
 }
 DEFAULT = "c2"
 HBM_PEAK_FALLBACK = 6800.0
@@ -88,6 +94,8 @@ def make_problem(w, seed, device, with_logk=False):
         off, A = I.OFF7, I.laplace7(d, device=device)
     elif w["gen"] == "q1":
         off, A = I.OFF27, I.q1_aniso27(d, seed, device=device)
+    elif w["gen"] == "q1z":
+        off, A = I.OFF27, I.q1_aniso27(d, seed, aniso=(1e-3, 1e-3, 1.0), device=device)
     elif w["gen"] == "fv":
         off, (A, logk) = I.OFF7, I.varcoef7(d, seed, device=device)
     else:
@@ -300,7 +308,12 @@ def run_ours(args, w, rank, world):
         rhs = b.float()
     ny = int(w["dims"][1])
     kfile = ("k_sweep3" if ny <= 512 else "k_sweep2") if B == 1 else ("k_bsweep3" if ny <= 512 else "k_sweep (3x3 blocks)")
-    if w["smoother"] == 1:
+    if w["smoother"] == 2:
+        op, kname = smg.OP_LGS_FORWARD, "k_lsweep (line Gauss-Seidel forward, level 0)"
+        flops_pt, bytes_pt = 2 * (nsf - 3) + 10, nsf * cbytes + 5 * 8 + 3 * vbytes
+        vec.zero_()
+        run_k = lambda: h.level_apply(0, op, x=vec, b=rhs)
+    elif w["smoother"] == 1:
         op, kname = smg.OP_ILU_LOWER, "%s (ILU(0) lower solve, level 0)" % kfile
         flops_pt, bytes_pt = 2 * nlow + 1, nlow * cbytes + 2 * vbytes + (4 if w["precision"] == 2 else 0)
         run_k = lambda: h.level_apply(0, op, b=rhs, y=vec)
@@ -438,12 +451,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     metric = "time to solution (set-up + Krylov to rel-res %g), %s" % (w["tol"], w["desc"])
     config = {"workload": w["desc"], "dims": list(w["dims"]), "unknowns_per_point": w.get("block", 1),
-              "smoother": ["sym-GS", "ILU(0)"][w["smoother"]], "transfer": ["3d27v", "3d8c", "3d64c interp. + 3d8c restr."][w["transfer"]],
+              "smoother": ["sym-GS", "ILU(0)", "sym-LGS (z-lines)"][w["smoother"]], "transfer": ["3d27v", "3d8c", "3d64c interp. + 3d8c restr."][w["transfer"]],
               "hierarchy_precision": ["fp64", "fp32", "bf16-rowscaled"][w["precision"]],
               "krylov": ["PCG", "FPCG", "FGMRES(30)"][w["krylov"]], "tol": w["tol"],
               "parallelism": "replicas" if args.gpus > 1 else "single-gpu",
               "l2": "inputs larger than L2 (matrix of %.1f GB)" % (
-                  w["dims"][0] * w["dims"][1] * w["dims"][2] * 8 * (27 if w["gen"] == "q1" else 7) *
+                  w["dims"][0] * w["dims"][1] * w["dims"][2] * 8 * (27 if w["gen"] in ("q1", "q1z") else 7) *
                   w.get("block", 1) ** 2 / 1e9)}
     if args.impl == "reference":
         if rank != 0:

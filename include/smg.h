@@ -48,7 +48,7 @@ typedef enum {
   SMG_ETIMEOUT = 7     /* a bounded device-side wait ran out */
 } smg_status;
 
-enum { SMG_SMOOTHER_SGS = 0, SMG_SMOOTHER_ILU0 = 1 };
+enum { SMG_SMOOTHER_SGS = 0, SMG_SMOOTHER_ILU0 = 1, SMG_SMOOTHER_LGS = 2 };
 enum { SMG_TRANSFER_FW27V = 0, SMG_TRANSFER_PC8C = 1, SMG_TRANSFER_C64C = 2 };
 enum { SMG_PREC_FP64 = 0, SMG_PREC_FP32 = 1, SMG_PREC_BF16 = 2 };
 enum { SMG_KRYLOV_PCG = 0, SMG_KRYLOV_FPCG = 1, SMG_KRYLOV_FGMRES = 2 };
@@ -59,6 +59,14 @@ enum { SMG_KRYLOV_PCG = 0, SMG_KRYLOV_FPCG = 1, SMG_KRYLOV_FGMRES = 2 };
  *                    ILU formula; Sec. 4.2 ILU masks).  One pre- and one
  *                    post-smoothing step per level (Sec. 5.2); the first
  *                    pre-smoothing starts from zero (ZeroGuess, Table 8).
+ *                    LGS: symmetric line Gauss-Seidel along z (Sec. 4.4 LGS):
+ *                    each z-column is updated at once, its couplings to other
+ *                    columns moved to the right-hand side and its tridiagonal
+ *                    system solved exactly; columns in lexicographic (x, y)
+ *                    order, then in reverse.  Requires block == 1, FP64,
+ *                    relax_w 1 and nz <= 1024 (else SMG_EINVAL); a column
+ *                    whose Thomas pivots are not all positive gives
+ *                    SMG_EBREAKDOWN.
  *  transfer   [FW27V] vertex full weighting: coarse I on fine 2I+1, trilinear
  *                    P and R = P^T/8 (Table 3 pattern 3d27v); PC8C: cell
  *                    piecewise constant, R(I,u)=1 on u in 2I+{0,1}^3, P = R^T
@@ -183,6 +191,9 @@ int smg_level_copy(smg_t h, int l, int which, void* dst, size_t bytes, size_t* n
  *  SMG_OP_COARSE_SOLVE y = A_c^{-1} b on the coarsest level (-, b, y), double
  *  SMG_OP_ILU_LOWER    y = L^{-1} b (unit lower solve only; y may equal b)
  *  SMG_OP_ILU_UPPER    y = U^{-1} b (upper solve only; y may equal b)
+ *  SMG_OP_LGS_FORWARD  x <- forward line sweep on A x = b    (x, b, -) in place
+ *  SMG_OP_LGS_BACKWARD x <- backward line sweep              (x, b, -) in place
+ *  SMG_OP_LGS_ZERO     x <- forward line sweep from x = 0    (x, b, -)
  * A one-level hierarchy keeps its smoother data, so the sweeps are available
  * on level 0 even when it is also the coarsest level.
  * Errors: SMG_EINVAL (bad level/op/missing smoother data), SMG_ECUDA,
@@ -190,7 +201,8 @@ int smg_level_copy(smg_t h, int l, int which, void* dst, size_t bytes, size_t* n
 enum {
   SMG_OP_SPMV = 0, SMG_OP_RESIDUAL = 1, SMG_OP_GS_FORWARD = 2, SMG_OP_GS_BACKWARD = 3, SMG_OP_GS_ZERO = 4,
   SMG_OP_ILU_APPLY = 5, SMG_OP_RESTRICT = 6, SMG_OP_PROLONG_ADD = 7, SMG_OP_COARSE_SOLVE = 8,
-  SMG_OP_ILU_LOWER = 9, SMG_OP_ILU_UPPER = 10
+  SMG_OP_ILU_LOWER = 9, SMG_OP_ILU_UPPER = 10, SMG_OP_LGS_FORWARD = 11, SMG_OP_LGS_BACKWARD = 12,
+  SMG_OP_LGS_ZERO = 13
 };
 int smg_level_apply(smg_t h, int l, int op, const void* x, const void* b, void* y, void* stream);
 

@@ -1,0 +1,541 @@
+// Line Gauss-Seidel along z (Sec. 4.4, LGS): the points of a z-column (i, j)
+// are updated together.  The column's right-hand side is b minus every
+// coupling to another column (columns earlier in the sweep already new,
+// later ones old, none of the later ones from a zero guess), and the
+// tridiagonal system of the offsets (0,0,-1), (0,0,0), (0,0,+1) is solved
+// exactly.  Columns run in lexicographic (i, j) order (reversed for the
+// backward sweep), scheduled like the point sweeps: one x-plane per CTA at a
+// time (atomic ticket), column j of plane i after column j + 1 (or j for a
+// 7-point mask) of plane i - 1, progress published by the wavefront engine's
+// publisher / poller warps.
+//
+// A column is solved by one warp.  The serial Thomas recurrence of the
+// paper would put 2 nz dependent FP64 operations on the critical path, so
+// the column is cut into 32 chunks of m rows, one per lane (partition
+// method): every lane eliminates its rows 2..m in terms of its own first
+// unknown P_L and the next chunk's first unknown P_{L+1}, the 32 chunk-first
+// unknowns form a tridiagonal system solved by parallel cyclic reduction
+// across the lanes, and each lane then recovers its rows.  Everything that
+// depends only on the matrix (reciprocal pivots, elimination multipliers,
+// the reduced system's PCR multipliers) is computed once at set-up, so a
+// sweep does no division.  In exact arithmetic the result is the Thomas
+// solution; the rounding differs.
+#include <cstdint>
+#include <utility>
+
+#include "shapes.cuh"
+#include "smg_internal.cuh"
+#include "wavefront.cuh"
+
+namespace {
+
+constexpr int kLgsWarps = 8;                       // compute warps of a CTA
+constexpr int kLgsThreads = (kLgsWarps + 2) * 32;  // + publisher + poller
+constexpr int kLgsMaxM = 32;                       // rows per chunk: nz <= 1024
+constexpr unsigned kFull = 0xffffffffu;
+
+// Column block of the line factors, in doubles, every field 32 lanes wide:
+// for chunk rows r = 1..m-1 the fields F_W (a_r / den_r), F_INV (1 / den_r),
+// F_CP (c_r / den_r), F_G, F_H (x_r = e_r - g_r P_{L+1} - h_r P_L); then per
+// chunk C_A0, C_C0 (the couplings of its first row), C_AL + t, C_GA + t (the
+// PCR multipliers of step t, stride 2^t) and C_INVB (1 / final pivot).
+enum { F_W, F_INV, F_CP, F_G, F_H, F_N };
+enum { C_A0 = 0, C_C0 = 1, C_AL = 2, C_GA = 7, C_INVB = 12, C_N = 13 };
+__host__ __device__ inline int lgs_row(int r, int f) { return ((r - 1) * F_N + f) * 32; }
+__host__ __device__ inline int lgs_chunk(int m, int f) { return ((m - 1) * F_N + f) * 32; }
+
+__device__ __forceinline__ void lgs_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kLgsWarps * 32) : "memory");
+}
+
+struct LineIdx {
+  int sub, diag, sup;  // stencil entries of (0,0,-1), (0,0,0), (0,0,+1); -1 if absent
+};
+
+// Tridiagonal coefficients of row k of column col (identity beyond nz).
+__device__ __forceinline__ void line_coef(const Grid& g, int ns, const LineIdx& e, const double* A, long long col,
+                                          int k, double& a, double& b, double& c) {
+  if (k >= g.nz) {
+    a = 0.0;
+    b = 1.0;
+    c = 0.0;
+    return;
+  }
+  const long long p = col * g.nz + k;
+  a = (k > 0 && e.sub >= 0) ? A[p * ns + e.sub] : 0.0;
+  b = A[p * ns + e.diag];
+  c = (k + 1 < g.nz && e.sup >= 0) ? A[p * ns + e.sup] : 0.0;
+}
+
+// The oracle's breakdown rule: every Thomas pivot of every column positive.
+__global__ void k_lgs_pivots(Grid g, int ns, LineIdx e, const double* __restrict__ A, int* err) {
+  const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= (long long)g.nx * g.ny) return;
+  double cprev = 0.0;
+  for (int k = 0; k < g.nz; ++k) {
+    double a, b, c;
+    line_coef(g, ns, e, A, col, k, a, b, c);
+    const double piv = b - a * cprev;
+    if (!(piv > 0.0)) {
+      atomicCAS(err, 0, SMG_EBREAKDOWN);
+      return;
+    }
+    cprev = c / piv;
+  }
+}
+
+// One warp per column, lane L = chunk L: the partitioned elimination of
+// rows L*m + 1 .. L*m + m-1 and the reduced system's PCR multipliers.
+__global__ void k_lgs_factor(Grid g, int ns, LineIdx e, const double* __restrict__ A, double* __restrict__ Fo, int m,
+                             long long blk, int* err) {
+  const long long col = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (col >= (long long)g.nx * g.ny) return;  // warp-uniform
+  const int L = threadIdx.x & 31;
+  double* F = Fo + col * blk;
+  double cp[kLgsMaxM], fp[kLgsMaxM];
+  bool bad = false;
+  for (int r = 1; r < m; ++r) {
+    double a, b, c;
+    line_coef(g, ns, e, A, col, L * m + r, a, b, c);
+    const double den = r == 1 ? b : b - a * cp[r - 1];
+    bad |= !(den > 0.0);
+    const double inv = 1.0 / den;
+    cp[r] = c * inv;
+    fp[r] = (r == 1 ? a : -a * fp[r - 1]) * inv;
+    F[lgs_row(r, F_W) + L] = a * inv;
+    F[lgs_row(r, F_INV) + L] = inv;
+    F[lgs_row(r, F_CP) + L] = cp[r];
+  }
+  double gg = cp[m - 1], hh = fp[m - 1];
+  const double glast = gg, hlast = hh;
+  F[lgs_row(m - 1, F_G) + L] = gg;
+  F[lgs_row(m - 1, F_H) + L] = hh;
+  for (int r = m - 2; r >= 1; --r) {
+    hh = fp[r] - cp[r] * hh;
+    gg = -cp[r] * gg;
+    F[lgs_row(r, F_G) + L] = gg;
+    F[lgs_row(r, F_H) + L] = hh;
+  }
+  // reduced row of chunk L in P_{L-1}, P_L, P_{L+1}
+  double a0, b0, c0;
+  line_coef(g, ns, e, A, col, L * m, a0, b0, c0);
+  double gl = __shfl_up_sync(kFull, glast, 1), hl = __shfl_up_sync(kFull, hlast, 1);
+  if (L == 0) gl = hl = 0.0;
+  double Ar = -a0 * hl;
+  double Br = b0 - a0 * gl - c0 * hh;  // hh, gg now hold h_1, g_1
+  double Cr = -c0 * gg;
+  F[lgs_chunk(m, C_A0) + L] = a0;
+  F[lgs_chunk(m, C_C0) + L] = c0;
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    const int s = 1 << t;
+    const double Am = __shfl_up_sync(kFull, Ar, s), Bm = __shfl_up_sync(kFull, Br, s),
+                 Cm = __shfl_up_sync(kFull, Cr, s);
+    const double Ap = __shfl_down_sync(kFull, Ar, s), Bp = __shfl_down_sync(kFull, Br, s),
+                 Cp = __shfl_down_sync(kFull, Cr, s);
+    const bool lo = L >= s, hi = L + s < 32;
+    const double al = lo ? -Ar / Bm : 0.0, ga = hi ? -Cr / Bp : 0.0;
+    const double nB = Br + (lo ? al * Cm : 0.0) + (hi ? ga * Ap : 0.0);
+    Ar = lo ? al * Am : 0.0;
+    Cr = hi ? ga * Cp : 0.0;
+    Br = nB;
+    F[lgs_chunk(m, C_AL + t) + L] = al;
+    F[lgs_chunk(m, C_GA + t) + L] = ga;
+  }
+  bad |= !(Br > 0.0);
+  F[lgs_chunk(m, C_INVB) + L] = 1.0 / Br;
+  if (bad) atomicCAS(err, 0, SMG_EBREAKDOWN);
+}
+
+struct LsParams {
+  Grid g;
+  WfCtl C;
+  Stencil s;
+  const double* A;
+  const double* F;
+  const double* b;
+  double* u;
+  int m;          // rows per chunk
+  long long blk;  // doubles per column block of F
+  int dep;        // previous-plane columns a column reads beyond its own (0 or 1)
+};
+
+// Asynchronous 16-byte global -> shared copies (completion per thread, in
+// commit groups).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shared-memory carve-up (doubles): rhs and x of the current column in the
+// chunk layout (chunk L, row r at L * (m + 1) + r), two buffers of the
+// column factors, and with STAGE two buffers of the column's matrix rows
+// [nz][ns] and right-hand side [nz].
+__host__ __device__ inline long long lgs_smem_doubles(int m, long long blk, int nz, int ns, bool stage) {
+  return 2LL * 32 * (m + 1) + 2 * blk + (stage ? 2LL * ((long long)nz * ns + nz) : 0);
+}
+
+// One off-column term of a point's right-hand side for a canonical mask
+// (compile-time offsets): acc -= a_E x_{p + o_E}.  The neighbour is read
+// unconditionally at a clamped address (its own point when off the grid, the
+// term then dropped), so all loads of a point can be issued together.
+template <int NS, int KIND, int DIR, int E>
+__device__ __forceinline__ void line_term(double (&acc)[4], const double* __restrict__ arow,
+                                          const double* __restrict__ up, const double* __restrict__ xs, int kc,
+                                          int kr, int m, int mp, const int* lin, unsigned xymask, unsigned zmask) {
+  using S = Shape<NS>;
+  constexpr int dx = S::o(E, 0), dy = S::o(E, 1), dz = S::o(E, 2);
+  constexpr bool in_column = dx == 0 && dy == 0;
+  constexpr bool earlier = DIR * dx < 0 || (dx == 0 && DIR * dy < 0);
+  if constexpr (!in_column && (KIND != SW_GS_ZERO || earlier)) {
+    const bool ok = ((xymask >> ((dx + 1) * 3 + (dy + 1))) & 1u) && ((zmask >> (dz + 1)) & 1u);
+    double x;
+    if constexpr (dx == 0 && dy == -DIR) {
+      // the previous column of the sweep, still in the x buffer (chunk layout)
+      int rc = kc, rr = kr + dz;
+      if (rr < 0) { rc -= 1; rr += m; }
+      if (rr >= m) { rc += 1; rr -= m; }
+      x = xs[ok ? rc * mp + rr : kc * mp + kr];
+    } else if constexpr (dx != 0) {
+      x = __ldcg(up + (ok ? lin[E] : 0));  // other planes: other CTAs' data, through L2
+    } else {
+      x = up[ok ? lin[E] : 0];
+    }
+    acc[E & 3] = fma(-arow[E], ok ? x : 0.0, acc[E & 3]);
+  }
+}
+
+template <int NS, int KIND, int DIR, int... Es>
+__device__ __forceinline__ void line_terms(double (&acc)[4], const double* __restrict__ arow,
+                                           const double* __restrict__ up, const double* __restrict__ xs, int kc,
+                                           int kr, int m, int mp, const int* lin, unsigned xymask, unsigned zmask,
+                                           std::integer_sequence<int, Es...>) {
+  (line_term<NS, KIND, DIR, Es>(acc, arow, up, xs, kc, kr, m, mp, lin, xymask, zmask), ...);
+}
+
+// STAGE: the next column's matrix rows and right-hand side are copied to
+// shared memory while the current one is solved (needs even nz, 16-byte
+// aligned A and b, and room); otherwise they are read from global memory.
+// Forward and backward elimination of rows 1..m-1 of lane L's chunk, the
+// PCR solve of the chunk-first unknowns and the recovery of the rows: x (in
+// the chunk layout) from the right-hand side d (overwritten).  The loads of
+// each group of four rows are issued before the dependent arithmetic.
+__device__ __forceinline__ void lgs_solve_column(double* __restrict__ d, double* __restrict__ x,
+                                                 const double* __restrict__ fc, int m, int L) {
+  const int mp = m + 1, base = L * mp;
+  double v = 0.0;
+  for (int r0 = 1; r0 < m; r0 += 4) {
+    double dv[4], iv[4], wv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + q;
+      if (r < m) {
+        dv[q] = d[base + r];
+        iv[q] = fc[lgs_row(r, F_INV) + L];
+        wv[q] = fc[lgs_row(r, F_W) + L];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + q;
+      if (r < m) {
+        // dp_r = d_r / den_r - (a_r / den_r) dp_{r-1}  (no dp_0 term in row 1)
+        v = r == 1 ? dv[q] * iv[q] : fma(-wv[q], v, dv[q] * iv[q]);
+        d[base + r] = v;
+      }
+    }
+  }
+  // backward: e_r = dp_r - c'_r e_{r+1}, from e_{m-1} = dp_{m-1} (= v)
+  for (int r0 = m - 2; r0 >= 1; r0 -= 4) {
+    double dv[4], cv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 - q;
+      if (r >= 1) {
+        dv[q] = d[base + r];
+        cv[q] = fc[lgs_row(r, F_CP) + L];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 - q;
+      if (r >= 1) {
+        v = fma(-cv[q], v, dv[q]);
+        d[base + r] = v;
+      }
+    }
+  }
+  double al[5], ga[5];
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    al[t] = fc[lgs_chunk(m, C_AL + t) + L];
+    ga[t] = fc[lgs_chunk(m, C_GA + t) + L];
+  }
+  const double a0 = fc[lgs_chunk(m, C_A0) + L], c0 = fc[lgs_chunk(m, C_C0) + L];
+  const double invb = fc[lgs_chunk(m, C_INVB) + L];
+  const double e1 = d[base + 1], elast = d[base + m - 1];
+  const double eprev = __shfl_up_sync(kFull, elast, 1);
+  double D = fma(-c0, e1, fma(-a0, L > 0 ? eprev : 0.0, d[base]));
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    const double Dm = __shfl_up_sync(kFull, D, 1 << t), Dp = __shfl_down_sync(kFull, D, 1 << t);
+    D = fma(al[t], Dm, fma(ga[t], Dp, D));
+  }
+  const double Pv = D * invb;
+  const double Pn = __shfl_down_sync(kFull, Pv, 1);
+  x[base] = Pv;
+  for (int r0 = 1; r0 < m; r0 += 4) {
+    double ev[4], gv[4], hv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + q;
+      if (r < m) {
+        ev[q] = d[base + r];
+        gv[q] = fc[lgs_row(r, F_G) + L];
+        hv[q] = fc[lgs_row(r, F_H) + L];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + q;
+      if (r < m) x[base + r] = fma(-gv[q], Pn, fma(-hv[q], Pv, ev[q]));
+    }
+  }
+}
+
+// STAGE: the next column's matrix rows and right-hand side are copied to
+// shared memory while the current one is solved (needs even nz, 16-byte
+// aligned A and b, and room); otherwise they are read from global memory.
+// NS = 7, 19, 27: the canonical mask of that size (compile-time offsets);
+// NS = 0: any mask, offsets read at run time.
+template <int NS, int KIND, int DIR, bool STAGE>
+__global__ void __launch_bounds__(kLgsThreads, 1) k_lsweep(LsParams P) {
+  __shared__ WfShared sh;
+  __shared__ int s_abort;
+  extern __shared__ __align__(16) double lgs_sm[];
+  const Grid g = P.g;
+  const int ns = P.s.ns;
+  const int m = P.m, mp = m + 1, nzp = 32 * m;
+  const long long blk = P.blk, na = (long long)g.nz * ns;
+  // shared-memory offsets (doubles): rhs and x in the chunk layout, two
+  // factor buffers, with STAGE two buffers of matrix rows and of b
+  const int o_rhs = 0, o_x = 32 * mp;
+  const long long o_fac = 64LL * mp, o_a = o_fac + 2 * blk, o_b = o_a + 2 * na;
+  const double* __restrict__ A = P.A;
+  const double* __restrict__ b = P.b;
+  double* u = P.u;
+  wf_run(
+      sh, P.C,
+      [&](int I) {
+        const int tid = threadIdx.x, lane = tid & 31;
+        const int i = DIR > 0 ? I : g.nx - 1 - I;
+        // copies of column Jn's data into buffer Jn & 1; always one commit group
+        auto prefetch = [&](int Jn) {
+          if (Jn < g.ny) {
+            const int jn = DIR > 0 ? Jn : g.ny - 1 - Jn;
+            const long long coln = (long long)i * g.ny + jn;
+            const int sel = Jn & 1;
+            const double* Fs = P.F + coln * blk;
+            double* Fd = lgs_sm + o_fac + sel * blk;
+            for (int q = 2 * tid; q < blk; q += 2 * kLgsWarps * 32) cp_async16(Fd + q, Fs + q);
+            if (STAGE) {
+              const double* As = A + coln * na;
+              double* Ad = lgs_sm + o_a + sel * na;
+              for (int q = 2 * tid; q < na; q += 2 * kLgsWarps * 32) cp_async16(Ad + q, As + q);
+              const double* bs = b + coln * g.nz;
+              double* bd = lgs_sm + o_b + sel * g.nz;
+              for (int q = 2 * tid; q < g.nz; q += 2 * kLgsWarps * 32) cp_async16(bd + q, bs + q);
+            }
+          }
+          cp_async_commit();
+        };
+        prefetch(0);
+        int have_left = kWfDone, have_up = INT_MIN;
+        for (int J = 0; J < g.ny; ++J) {
+          const int j = DIR > 0 ? J : g.ny - 1 - J;
+          const int sel = J & 1;
+          prefetch(J + 1);
+          if (tid < 32) {
+            const int ab = wf_wait(sh, P.C, 0, J, min(J + 1 + P.dep, g.ny), have_left, have_up, lane);
+            if (lane == 0) s_abort = ab;
+          }
+          cp_async_wait<1>();  // this thread's copies of column J have landed
+          lgs_bar();
+          if (s_abort) break;
+          unsigned xymask = 0;
+#pragma unroll
+          for (int a = -1; a <= 1; ++a)
+#pragma unroll
+            for (int c = -1; c <= 1; ++c)
+              if ((unsigned)(i + a) < (unsigned)g.nx && (unsigned)(j + c) < (unsigned)g.ny)
+                xymask |= 1u << ((a + 1) * 3 + (c + 1));
+          const long long colbase = ((long long)i * g.ny + j) * g.nz;
+          const long long oa = o_a + sel * na, ob = o_b + sel * g.nz;
+          // right-hand side: b minus the couplings to other columns; the
+          // previous column of the sweep is still in the x buffer
+          for (int k = tid; k < nzp; k += kLgsWarps * 32) {
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            const int kc = k / m, kr = k - kc * m;
+            if (k < g.nz) {
+              const long long p = colbase + k;
+              acc[0] = STAGE ? lgs_sm[ob + k] : b[p];
+              const unsigned zmask = (k > 0 ? 1u : 0u) | 2u | (k + 1 < g.nz ? 4u : 0u);
+              if constexpr (NS > 0) {
+                const double* arow = STAGE ? lgs_sm + oa + (long long)k * NS : A + p * NS;
+                line_terms<NS, KIND, DIR>(acc, arow, u + p, lgs_sm + o_x, kc, kr, m, mp, P.s.lin, xymask, zmask,
+                                          std::make_integer_sequence<int, NS>{});
+              } else {
+#pragma unroll 1
+              for (int e = 0; e < ns; ++e) {
+                const int dx = P.s.off[e][0], dy = P.s.off[e][1], dz = P.s.off[e][2];
+                if (dx == 0 && dy == 0) continue;
+                if (KIND == SW_GS_ZERO && !(DIR * dx < 0 || (dx == 0 && DIR * dy < 0))) continue;
+                if (!((xymask >> ((dx + 1) * 3 + (dy + 1))) & 1u) || !((zmask >> (dz + 1)) & 1u)) continue;
+                double x;
+                if (dx == 0 && dy == -DIR) {
+                  // row k + dz of the chunk layout: same chunk unless it crosses an edge
+                  int rc = kc, rr = kr + dz;
+                  if (rr < 0) { rc -= 1; rr += m; }
+                  if (rr >= m) { rc += 1; rr -= m; }
+                  x = lgs_sm[o_x + rc * mp + rr];
+                } else if (dx != 0) {
+                  x = __ldcg(u + p + P.s.lin[e]);  // other planes: other CTAs' data, through L2
+                } else {
+                  x = u[p + P.s.lin[e]];
+                }
+                const double a = STAGE ? lgs_sm[oa + (long long)k * ns + e] : __ldg(A + p * ns + e);
+                acc[e & 3] = fma(-a, x, acc[e & 3]);
+              }
+              }
+            }
+            lgs_sm[o_rhs + kc * mp + kr] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+          }
+          lgs_bar();
+          if (tid < 32) lgs_solve_column(lgs_sm + o_rhs, lgs_sm + o_x, lgs_sm + o_fac + sel * blk, m, lane);
+          lgs_bar();
+          for (int k = tid; k < g.nz; k += kLgsWarps * 32) {
+            const int kc = k / m;
+            u[colbase + k] = lgs_sm[o_x + kc * mp + (k - kc * m)];
+          }
+          lgs_bar();  // the column's stores precede the release below
+          if (tid == 0) wf_st_rel_cta(&sh.wdone[0], J + 1);
+        }
+        cp_async_wait<0>();  // no copy may land after the CTA moves on
+        lgs_bar();
+        if (tid == 0) wf_st_rel_cta(&sh.wdone[0], kWfDone);
+      },
+      kLgsWarps);
+}
+
+LineIdx line_idx(const Stencil& s) {
+  LineIdx e{-1, -1, -1};
+  for (int t = 0; t < s.ns; ++t) {
+    if (s.off[t][0] != 0 || s.off[t][1] != 0) continue;
+    if (s.off[t][2] == -1) e.sub = t;
+    if (s.off[t][2] == 0) e.diag = t;
+    if (s.off[t][2] == 1) e.sup = t;
+  }
+  return e;
+}
+
+constexpr size_t kLgsMaxSmem = 200 * 1024;
+
+template <int NS>
+bool canonical_mask(const Stencil& s) {
+  if (s.ns != NS) return false;
+  for (int e = 0; e < NS; ++e)
+    for (int d = 0; d < 3; ++d)
+      if (s.off[e][d] != Shape<NS>::o(e, d)) return false;
+  return true;
+}
+
+template <int NSMAX, bool STAGE>
+cudaError_t launch_ns(int kind, int dir, const LsParams& P, int grid, size_t smem, cudaStream_t st) {
+  auto go = [&](auto kern) {
+    cudaError_t a = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (a != cudaSuccess) return a;
+    kern<<<grid, kLgsThreads, smem, st>>>(P);
+    return cudaGetLastError();
+  };
+  if (kind == SW_GS_ZERO)
+    return dir > 0 ? go(k_lsweep<NSMAX, SW_GS_ZERO, 1, STAGE>) : go(k_lsweep<NSMAX, SW_GS_ZERO, -1, STAGE>);
+  return dir > 0 ? go(k_lsweep<NSMAX, SW_GS_FULL, 1, STAGE>) : go(k_lsweep<NSMAX, SW_GS_FULL, -1, STAGE>);
+}
+
+template <int NSMAX>
+cudaError_t launch_stage(bool stage, int kind, int dir, const LsParams& P, int grid, size_t smem, cudaStream_t st) {
+  return stage ? launch_ns<NSMAX, true>(kind, dir, P, grid, smem, st)
+               : launch_ns<NSMAX, false>(kind, dir, P, grid, smem, st);
+}
+
+}  // namespace
+
+int lgs_chunk_rows(int nz) {
+  const int m = (nz + 31) / 32;
+  return m < 2 ? 2 : m;
+}
+
+long long lgs_block_doubles(int nz) { return (long long)((lgs_chunk_rows(nz) - 1) * F_N + C_N) * 32; }
+
+bool lgs_supported(const Grid& g, const Stencil& s) {
+  const LineIdx e = line_idx(s);
+  return e.diag >= 0 && lgs_chunk_rows(g.nz) <= kLgsMaxM && (size_t)g.nx <= (size_t)kProgSlots;
+}
+
+cudaError_t launch_lgs_setup(const Grid& g, const Stencil& s, const double* A, double* F, int* err,
+                             cudaStream_t st) {
+  if (!lgs_supported(g, s)) return cudaErrorNotSupported;
+  const LineIdx e = line_idx(s);
+  const long long ncol = (long long)g.nx * g.ny;
+  k_lgs_pivots<<<div_up(ncol, 128), 128, 0, st>>>(g, s.ns, e, A, err);
+  cudaError_t r = cudaGetLastError();
+  if (r != cudaSuccess) return r;
+  k_lgs_factor<<<div_up(ncol * 32, 128), 128, 0, st>>>(g, s.ns, e, A, F, lgs_chunk_rows(g.nz),
+                                                        lgs_block_doubles(g.nz), err);
+  smg_count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lsweep(const Grid& g, const Stencil& s, int kind, int dir, const double* A, const double* F,
+                          const double* b, double* u, SweepWs* ws, int* err, unsigned long long budget_ns,
+                          cudaStream_t st) {
+  if (!lgs_supported(g, s) || (kind != SW_GS_ZERO && kind != SW_GS_FULL)) return cudaErrorNotSupported;
+  int dev = 0, nsm = 0;
+  cudaError_t r = cudaGetDevice(&dev);
+  if (r == cudaSuccess) r = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (r != cudaSuccess) return r;
+  LsParams P;
+  P.g = g;
+  P.C = WfCtl{g.nx, 1, 0, 0, budget_ns, ws, err};
+  P.s = s;
+  P.A = A;
+  P.F = F;
+  P.b = b;
+  P.u = u;
+  P.m = lgs_chunk_rows(g.nz);
+  P.blk = lgs_block_doubles(g.nz);
+  // previous-plane columns read beyond the current one, in sweep order
+  P.dep = 0;
+  for (int t = 0; t < s.ns; ++t)
+    if (dir * s.off[t][0] == -1) P.dep = std::max(P.dep, dir * s.off[t][1]);
+  // stage the matrix rows and right-hand side of the next column in shared
+  // memory when the 16-byte copies line up and both buffers fit
+  const bool stage = g.nz % 2 == 0 && ((uintptr_t)A % 16) == 0 && ((uintptr_t)b % 16) == 0 &&
+                     lgs_smem_doubles(P.m, P.blk, g.nz, s.ns, true) * sizeof(double) <= kLgsMaxSmem;
+  // one CTA per SM: the reservation exceeds half of the SM's shared memory
+  const size_t smem =
+      std::max(kWfOneCtaPerSmSmem, (size_t)lgs_smem_doubles(P.m, P.blk, g.nz, s.ns, stage) * sizeof(double));
+  const int grid = std::min(g.nx, nsm);
+  if (canonical_mask<7>(s)) r = launch_stage<7>(stage, kind, dir, P, grid, smem, st);
+  else if (canonical_mask<19>(s)) r = launch_stage<19>(stage, kind, dir, P, grid, smem, st);
+  else if (canonical_mask<27>(s)) r = launch_stage<27>(stage, kind, dir, P, grid, smem, st);
+  else r = launch_stage<0>(stage, kind, dir, P, grid, smem, st);
+  smg_count_launch(1);
+  return r;
+}

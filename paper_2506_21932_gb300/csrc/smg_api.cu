@@ -72,6 +72,7 @@ struct Level {
   SweepWs* ws = nullptr;
   SweepCfg cfg{};
   int* ilu_upd = nullptr;
+  double* lf = nullptr;     // line Gauss-Seidel: per-column factors
 };
 
 struct smg_ctx {
@@ -209,8 +210,18 @@ static int sweep(smg_ctx* h, Level& L, int kind, int dir, const void* b, void* u
   return SMG_OK;
 }
 
+// One line Gauss-Seidel sweep (FP64 hierarchy only).
+static int lsweep(smg_ctx* h, Level& L, int kind, int dir, const void* b, void* u, cudaStream_t st) {
+  SMG_CUDA_TRY(launch_lsweep(L.g, L.s, kind, dir, L.A, L.lf, (const double*)b, (double*)u, L.ws, h->err,
+                             L.cfg.budget_ns, st));
+  return SMG_OK;
+}
+
 static int smooth_pre(smg_ctx* h, Level& L, const void* f, void* u, cudaStream_t st) {
-  if (h->opt.smoother == SMG_SMOOTHER_SGS) {
+  if (h->opt.smoother == SMG_SMOOTHER_LGS) {
+    TRY(lsweep(h, L, SW_GS_ZERO, +1, f, u, st));
+    TRY(lsweep(h, L, SW_GS_FULL, -1, f, u, st));
+  } else if (h->opt.smoother == SMG_SMOOTHER_SGS) {
     TRY(sweep(h, L, SW_GS_ZERO, +1, f, u, st));
     TRY(sweep(h, L, SW_GS_FULL, -1, f, u, st));
   } else {
@@ -221,7 +232,10 @@ static int smooth_pre(smg_ctx* h, Level& L, const void* f, void* u, cudaStream_t
 }
 
 static int smooth_post(smg_ctx* h, Level& L, const void* f, void* u, cudaStream_t st) {
-  if (h->opt.smoother == SMG_SMOOTHER_SGS) {
+  if (h->opt.smoother == SMG_SMOOTHER_LGS) {
+    TRY(lsweep(h, L, SW_GS_FULL, +1, f, u, st));
+    TRY(lsweep(h, L, SW_GS_FULL, -1, f, u, st));
+  } else if (h->opt.smoother == SMG_SMOOTHER_SGS) {
     TRY(sweep(h, L, SW_GS_FULL, +1, f, u, st));
     TRY(sweep(h, L, SW_GS_FULL, -1, f, u, st));
   } else {
@@ -402,7 +416,11 @@ static int setup_level_smoother(smg_ctx* h, Level& L, cudaStream_t st) {
   L.cfg.budget_ns = (unsigned long long)h->opt.spin_budget_ms * 1000000ull;
   TRY(dalloc(h, &L.ws, 1));
   SMG_CUDA_TRY(cudaMemsetAsync(L.ws, 0, sizeof(SweepWs), st));
-  if (h->opt.smoother == SMG_SMOOTHER_SGS) {
+  if (h->opt.smoother == SMG_SMOOTHER_LGS) {
+    if (!lgs_supported(L.g, L.s)) return SMG_EINVAL;
+    TRY(dalloc(h, &L.lf, (long long)L.g.nx * L.g.ny * lgs_block_doubles(L.g.nz)));
+    SMG_CUDA_TRY(launch_lgs_setup(L.g, L.s, L.A, L.lf, h->err, st));
+  } else if (h->opt.smoother == SMG_SMOOTHER_SGS) {
     TRY(dalloc(h, &L.dinv, n * B * B));
     SMG_CUDA_TRY(launch_diag_inverse(L.g, L.s, B, L.A, L.dinv, h->err, st));
   } else {
@@ -470,7 +488,11 @@ static void compute_stats(smg_ctx* h) {
     const int ns = L.s.ns, nlow = L.s.ec, nup = ns - 1 - L.s.ec;
     // per point, each array touched once per kernel
     double bpt = 0, fpt = 0;
-    if (h->opt.smoother == SMG_SMOOTHER_SGS) {
+    if (h->opt.smoother == SMG_SMOOTHER_LGS) {
+      // four line sweeps: the matrix row, 5 line factors, b, u read + write
+      bpt += 4 * (ns * c + 5 * 8.0 + 3 * v);
+      fpt += 4 * (2 * (ns - 3) + 10);
+    } else if (h->opt.smoother == SMG_SMOOTHER_SGS) {
       bpt += nlow * c * bb + cd * bb + 2 * v * B + s;                    // GS_ZERO forward
       bpt += 3 * ((ns - 1) * c * bb + cd * bb + 3 * v * B + s);          // three full sweeps
       fpt += 2 * (nlow * bb + bb) + 3 * 2 * ((ns - 1) * bb + bb);
@@ -629,7 +651,7 @@ extern "C" int smg_setup(smg_t* out, const int dims[3], int nstencil, const int*
   TRY(validate_mask(nstencil, offsets));
   smg_options o{};
   if (opt) o = *opt;
-  if (o.smoother < 0 || o.smoother > 1 || o.transfer < 0 || o.transfer > 2 || o.precision < 0 || o.precision > 2 ||
+  if (o.smoother < 0 || o.smoother > 2 || o.transfer < 0 || o.transfer > 2 || o.precision < 0 || o.precision > 2 ||
       o.krylov < 0 || o.krylov > 2)
     return SMG_EINVAL;
   if (o.restart == 0) o.restart = 30;
@@ -640,6 +662,10 @@ extern "C" int smg_setup(smg_t* out, const int dims[3], int nstencil, const int*
   if (o.spin_budget_ms <= 0) o.spin_budget_ms = 1000;
   if (block == 3 && (o.smoother != SMG_SMOOTHER_SGS || o.precision == SMG_PREC_BF16)) return SMG_EINVAL;
   if (o.smoother == SMG_SMOOTHER_ILU0 && nstencil != 7 && nstencil != 19 && nstencil != 27) return SMG_EINVAL;
+  // line Gauss-Seidel: scalar FP64 hierarchy, weight 1, columns of at most 1024 points
+  if (o.smoother == SMG_SMOOTHER_LGS &&
+      (block != 1 || o.precision != SMG_PREC_FP64 || o.relax_w != 1.0 || dims[2] > 1024))
+    return SMG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   smg_ctx* h = new smg_ctx();
   h->opt = o;
@@ -918,6 +944,13 @@ extern "C" int smg_level_apply(smg_t h, int l, int op, const void* x, const void
       if (!has_sm || h->opt.smoother != SMG_SMOOTHER_SGS || !x || !b) return SMG_EINVAL;
       TRY(sweep(h, L, op == SMG_OP_GS_ZERO ? SW_GS_ZERO : SW_GS_FULL, op == SMG_OP_GS_BACKWARD ? -1 : +1, b,
                 (void*)x, st));
+      break;
+    case SMG_OP_LGS_FORWARD:
+    case SMG_OP_LGS_BACKWARD:
+    case SMG_OP_LGS_ZERO:
+      if (!has_sm || h->opt.smoother != SMG_SMOOTHER_LGS || !x || !b) return SMG_EINVAL;
+      TRY(lsweep(h, L, op == SMG_OP_LGS_ZERO ? SW_GS_ZERO : SW_GS_FULL, op == SMG_OP_LGS_BACKWARD ? -1 : +1, b,
+                 (void*)x, st));
       break;
     case SMG_OP_ILU_APPLY:
       if (!has_sm || h->opt.smoother != SMG_SMOOTHER_ILU0 || !b || !y) return SMG_EINVAL;

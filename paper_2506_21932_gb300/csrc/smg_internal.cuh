@@ -202,6 +202,22 @@ cudaError_t launch_ilu_factor3(Grid g, const Stencil& s, double* LU, double* udi
 cudaError_t launch_ilu_factor(Grid g, const Stencil& s, const double* A, double* LU, double* udinv,
                               const int* upd, int nupd, SweepWs* ws, int* err, const SweepCfg& cfg, cudaStream_t st);
 
+// Line Gauss-Seidel along z (FP64, one unknown per point).  A column of nz
+// points is solved by one warp in 32 chunks of lgs_chunk_rows(nz) rows; its
+// matrix-only factors take lgs_block_doubles(nz) doubles per column, columns
+// in (i, j) order.  lgs_supported: the mask holds the centre and nz <= 1024.
+int lgs_chunk_rows(int nz);
+long long lgs_block_doubles(int nz);
+bool lgs_supported(const Grid& g, const Stencil& s);
+// Checks every column's Thomas pivots (SMG_EBREAKDOWN in *err unless all are
+// positive) and writes the factors F of every column.
+cudaError_t launch_lgs_setup(const Grid& g, const Stencil& s, const double* A, double* F, int* err, cudaStream_t st);
+// One forward (dir = +1) or backward (dir = -1) line sweep in place on u,
+// kind SW_GS_FULL, or SW_GS_ZERO (the later columns are left out).
+cudaError_t launch_lsweep(const Grid& g, const Stencil& s, int kind, int dir, const double* A, const double* F,
+                          const double* b, double* u, SweepWs* ws, int* err, unsigned long long budget_ns,
+                          cudaStream_t st);
+
 // Inverse diagonal (scalar 1/a_pp, or 3x3 block inverse); sets *err to
 // SMG_EBREAKDOWN on a zero pivot.
 cudaError_t launch_diag_inverse(Grid g, const Stencil& s, int B, const double* A, double* dinv, int* err,

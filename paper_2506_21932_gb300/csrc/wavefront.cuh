@@ -157,11 +157,13 @@ __device__ __forceinline__ void wf_done(WfShared& sh, int w, int s, int lane) {
 }
 
 // The persistent plane loop.  compute(I) runs on the compute warps of each
-// claimed plane (warps 0..NW-1), the publisher and poller on warps NW, NW+1.
-// The last CTA to leave resets the ticket and the counters it used.
+// claimed plane (warps 0..ncompute-1, by default one per progress counter,
+// ncompute = NW), the publisher and poller on the next two warps.  The last
+// CTA to leave resets the ticket and the counters it used.
 template <typename Compute>
-__device__ __forceinline__ void wf_run(WfShared& sh, const WfCtl& C, Compute compute) {
+__device__ __forceinline__ void wf_run(WfShared& sh, const WfCtl& C, Compute compute, int ncompute = -1) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (ncompute < 0) ncompute = C.NW;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -177,9 +179,9 @@ __device__ __forceinline__ void wf_run(WfShared& sh, const WfCtl& C, Compute com
       sh.avail[threadIdx.x] = (I == 0) ? kWfDone : 0;
     }
     __syncthreads();
-    if (warp == C.NW) wf_publish(sh, C, I, C.SA * I, lane);
-    else if (warp == C.NW + 1) wf_poll(sh, C, I, lane);
-    else if (warp < C.NW) compute(I);
+    if (warp == ncompute) wf_publish(sh, C, I, C.SA * I, lane);
+    else if (warp == ncompute + 1) wf_poll(sh, C, I, lane);
+    else if (warp < ncompute) compute(I);
   }
   if (threadIdx.x == 0) {
     __threadfence();

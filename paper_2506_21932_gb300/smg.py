@@ -12,12 +12,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsmg.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENOTCONV, ENAN, ETIMEOUT = range(8)
-SGS, ILU0 = 0, 1
+SGS, ILU0, LGS = 0, 1, 2
 FW27V, PC8C, C64C = 0, 1, 2
 FP64, FP32, BF16 = 0, 1, 2
 PCG, FPCG, FGMRES = 0, 1, 2
 OP_SPMV, OP_RESIDUAL, OP_GS_FORWARD, OP_GS_BACKWARD, OP_GS_ZERO, OP_ILU_APPLY, OP_RESTRICT, OP_PROLONG_ADD, \
-    OP_COARSE_SOLVE, OP_ILU_LOWER, OP_ILU_UPPER = range(11)
+    OP_COARSE_SOLVE, OP_ILU_LOWER, OP_ILU_UPPER, OP_LGS_FORWARD, OP_LGS_BACKWARD, OP_LGS_ZERO = range(14)
 ARR_A, ARR_LU, ARR_DINV, ARR_AV, ARR_AS, ARR_LUV, ARR_LS, ARR_US, ARR_DINV32 = range(9)
 LOSS_ERROR, LOSS_RESIDUAL = 0, 1
 
