@@ -17,7 +17,7 @@ _lib = None
 
 ORC_OK, ORC_EINVAL, ORC_ENOMEM, ORC_EBREAKDOWN, ORC_ENOTCONV, ORC_ENAN = 0, 1, 2, 4, 5, 6
 SGS, ILU0, LGS = 0, 1, 2
-FW27V, PC8C, C64C = 0, 1, 2
+FW27V, PC8C, C64C, C16XY = 0, 1, 2, 3
 FP64, FP32, BF16 = 0, 1, 2
 
 
@@ -140,13 +140,14 @@ def ilu0_apply(d, off, LU, Udinv, r):
     return x
 
 
-def coarse_dims(d):
-    return [int(t) // 2 for t in d]
+def coarse_dims(d, transfer=0):
+    """Coarse grid: every dimension halved (z kept by the x-y semi-coarsening, transfer 3)."""
+    return [int(t) if (transfer == 3 and a == 2) else int(t) // 2 for a, t in enumerate(d)]
 
 
 def restrict(transfer, fd, rf, B=1):
     fd, rf = _i3(fd), _f64(rf)
-    fc = np.zeros(npts(coarse_dims(fd)) * B)
+    fc = np.zeros(npts(coarse_dims(fd, transfer)) * B)
     lib().orc_restrict(transfer, _p(fd), B, _p(rf), _p(fc))
     return fc
 
@@ -161,7 +162,7 @@ def prolong_add(transfer, fd, ec, uf, B=1):
 def rap27(transfer, fd, off, Af, B=1):
     """Brute-force Galerkin product.  Returns (Ac27 [nc,27,B,B], present[27])."""
     fd, o, Af = _i3(fd), _offs(off), _f64(Af)
-    nc = npts(coarse_dims(fd))
+    nc = npts(coarse_dims(fd, transfer))
     Ac = np.zeros(nc * 27 * B * B)
     present = np.zeros(27, dtype=np.int32)
     rc = lib().orc_rap27(transfer, _p(fd), len(o), _p(o), B, _p(Af), _p(Ac), _p(present))
@@ -194,10 +195,10 @@ def bf16_round(x):
     return lib().orc_bf16_round(float(x))
 
 
-def plan_levels(d, max_levels=16):
+def plan_levels(d, max_levels=16, transfer=0):
     d = _i3(d)
     out = np.zeros((16, 3), dtype=np.int32)
-    L = lib().orc_plan_levels(_p(d), max_levels, _p(out))
+    L = lib().orc_plan_levels_t(transfer, _p(d), max_levels, _p(out))
     return [tuple(int(t) for t in out[l]) for l in range(L)]
 
 

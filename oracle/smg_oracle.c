@@ -385,11 +385,21 @@ void orc_ilu0_apply(const int d[3], int ns, const int* off, const double* LU, co
  *   cells 2J + {-1,0,1,2}^3 (hence "3d64c"), every fine cell takes 8 coarse
  *   cells.  Coarse cells off the grid are dropped (their weight is lost, as
  *   for the vertex transfer).  R is not a multiple of P^T, so A^C is in
- *   general nonsymmetric. */
+ *   general nonsymmetric.
+ * Transfer 3 = 2-D semi-coarsening in x and y (the weather setting of
+ *   Table 8: 2-D semi-coarsening, R 2d4c, P 2d16c): the x and y dimensions
+ *   are coarsened as in transfer 2 (restriction = sum over the 2 x 2 fine
+ *   cells of a coarse cell, interpolation = cell-centred bilinear with the
+ *   weights c above, coarse cells off the grid dropped), z is kept: coarse
+ *   point (I, J, K) owns fine points (2I + {0,1}, 2J + {0,1}, K). */
 
-void orc_coarse_dims(const int f[3], int c[3]) {
-  for (int t = 0; t < 3; ++t) c[t] = f[t] / 2;
+/* coarse grid of a fine grid: halved in every dimension, or in x and y only
+ * for the semi-coarsening transfer 3 */
+void orc_coarse_dims_t(int transfer, const int f[3], int c[3]) {
+  for (int t = 0; t < 3; ++t) c[t] = (transfer == 3 && t == 2) ? f[t] : f[t] / 2;
 }
+
+void orc_coarse_dims(const int f[3], int c[3]) { orc_coarse_dims_t(0, f, c); }
 
 static double w1(int dlt) { return dlt == 0 ? 1.0 : (dlt == 1 || dlt == -1 ? 0.5 : 0.0); }
 
@@ -400,6 +410,7 @@ static double wc(int d) { return (d == 0 || d == 1) ? 0.75 : ((d == -1 || d == 2
 static double pweight(int transfer, const int* v, const int* J) {
   if (transfer == 0) return w1(v[0] - (2 * J[0] + 1)) * w1(v[1] - (2 * J[1] + 1)) * w1(v[2] - (2 * J[2] + 1));
   if (transfer == 2) return wc(v[0] - 2 * J[0]) * wc(v[1] - 2 * J[1]) * wc(v[2] - 2 * J[2]);
+  if (transfer == 3) return v[2] == J[2] ? wc(v[0] - 2 * J[0]) * wc(v[1] - 2 * J[1]) : 0.0;
   for (int t = 0; t < 3; ++t)
     if (v[t] - 2 * J[t] < 0 || v[t] - 2 * J[t] > 1) return 0.0;
   return 1.0;
@@ -407,30 +418,41 @@ static double pweight(int transfer, const int* v, const int* J) {
 
 /* R(I,u) */
 static double rweight(int transfer, const int* I, const int* u) {
+  if (transfer == 3) {
+    for (int t = 0; t < 2; ++t)
+      if (u[t] - 2 * I[t] < 0 || u[t] - 2 * I[t] > 1) return 0.0;
+    return u[2] == I[2] ? 1.0 : 0.0;
+  }
   return transfer == 0 ? pweight(0, u, I) / 8.0 : pweight(1, u, I); /* transfers 1 and 2: 3d8c */
 }
 
-/* fine points that the coarse point I touches: base + [0, span)^3 */
-static void support(int transfer, const int* I, int base[3], int* span) {
-  for (int t = 0; t < 3; ++t) base[t] = transfer == 0 ? 2 * I[t] : 2 * I[t];
-  *span = transfer == 0 ? 3 : 2;
+/* fine points that the coarse point I touches: base[t] + [0, span[t]) */
+static void support(int transfer, const int* I, int base[3], int span[3]) {
+  for (int t = 0; t < 3; ++t) {
+    const int keep = transfer == 3 && t == 2; /* semi-coarsening keeps z */
+    base[t] = keep ? I[t] : 2 * I[t];
+    span[t] = keep ? 1 : (transfer == 0 ? 3 : 2);
+  }
 }
+
+/* the coarse coordinate a fine coordinate v[t] lies next to */
+static int coarse_of(int transfer, int t, int v) { return (transfer == 3 && t == 2) ? v : v / 2; }
 
 /* fc = R rf (B unknowns per point, each restricted separately). */
 void orc_restrict(int transfer, const int fd[3], int B, const double* rf, double* fc) {
   int cd[3];
-  orc_coarse_dims(fd, cd);
+  orc_coarse_dims_t(transfer, fd, cd);
   for (int I0 = 0; I0 < cd[0]; ++I0)
     for (int I1 = 0; I1 < cd[1]; ++I1)
       for (int I2 = 0; I2 < cd[2]; ++I2) {
-        int I[3] = {I0, I1, I2}, base[3], span;
-        support(transfer, I, base, &span);
+        int I[3] = {I0, I1, I2}, base[3], span[3];
+        support(transfer, I, base, span);
         long P = pidx(cd, I0, I1, I2);
         for (int r = 0; r < B; ++r) {
           double s = 0.0;
-          for (int a = 0; a < span; ++a)
-            for (int b = 0; b < span; ++b)
-              for (int c = 0; c < span; ++c) {
+          for (int a = 0; a < span[0]; ++a)
+            for (int b = 0; b < span[1]; ++b)
+              for (int c = 0; c < span[2]; ++c) {
                 int u[3] = {base[0] + a, base[1] + b, base[2] + c};
                 if (!inside(fd, u[0], u[1], u[2])) continue;
                 s += rweight(transfer, I, u) * rf[pidx(fd, u[0], u[1], u[2]) * B + r];
@@ -443,7 +465,7 @@ void orc_restrict(int transfer, const int fd[3], int B, const double* rf, double
 /* uf += P ec */
 void orc_prolong_add(int transfer, const int fd[3], int B, const double* ec, double* uf) {
   int cd[3];
-  orc_coarse_dims(fd, cd);
+  orc_coarse_dims_t(transfer, fd, cd);
   for (int v0 = 0; v0 < fd[0]; ++v0)
     for (int v1 = 0; v1 < fd[1]; ++v1)
       for (int v2 = 0; v2 < fd[2]; ++v2) {
@@ -451,11 +473,12 @@ void orc_prolong_add(int transfer, const int fd[3], int B, const double* ec, dou
         long q = pidx(fd, v0, v1, v2);
         for (int r = 0; r < B; ++r) {
           double s = 0.0;
-          /* every coarse J with a nonzero weight lies within 1 of v/2 */
+          /* every coarse J with a nonzero weight lies within 1 of v's coarse point */
           for (int a = -1; a <= 1; ++a)
             for (int b = -1; b <= 1; ++b)
               for (int c = -1; c <= 1; ++c) {
-                int J[3] = {v0 / 2 + a, v1 / 2 + b, v2 / 2 + c};
+                int J[3] = {coarse_of(transfer, 0, v0) + a, coarse_of(transfer, 1, v1) + b,
+                            coarse_of(transfer, 2, v2) + c};
                 if (!inside(cd, J[0], J[1], J[2])) continue;
                 double wgt = pweight(transfer, v, J);
                 if (wgt == 0.0) continue;
@@ -481,11 +504,11 @@ void orc_prolong_add(int transfer, const int fd[3], int B, const double* ec, dou
 /* All chains of one coarse point I, accumulated into out27[27][B][B]. */
 static int rap_point(int transfer, const int fd[3], const int cd[3], int ns, const int* off, int B, const double* Af,
                      const int I[3], double* out27, int* present) {
-  int base[3], span;
-  support(transfer, I, base, &span);
-  for (int a = 0; a < span; ++a)
-    for (int b = 0; b < span; ++b)
-      for (int c = 0; c < span; ++c) {
+  int base[3], span[3];
+  support(transfer, I, base, span);
+  for (int a = 0; a < span[0]; ++a)
+    for (int b = 0; b < span[1]; ++b)
+      for (int c = 0; c < span[2]; ++c) {
         int u[3] = {base[0] + a, base[1] + b, base[2] + c};
         if (!inside(fd, u[0], u[1], u[2])) continue;
         double wr = rweight(transfer, I, u);
@@ -516,7 +539,7 @@ static int rap_point(int transfer, const int fd[3], const int cd[3], int ns, con
 int orc_rap27(int transfer, const int fd[3], int ns, const int* off, int B, const double* Af, double* Ac27,
               int* present) {
   int cd[3];
-  orc_coarse_dims(fd, cd);
+  orc_coarse_dims_t(transfer, fd, cd);
   long nc = npts(cd);
   memset(Ac27, 0, sizeof(double) * nc * 27 * B * B);
   for (int o = 0; o < 27; ++o) present[o] = 0;
@@ -536,7 +559,7 @@ int orc_rap27(int transfer, const int fd[3], int ns, const int* off, int B, cons
 int orc_rap27_at(int transfer, const int fd[3], int ns, const int* off, int B, const double* Af, long npoints,
                  const long* points, double* out27) {
   int cd[3], present[27];
-  orc_coarse_dims(fd, cd);
+  orc_coarse_dims_t(transfer, fd, cd);
   memset(out27, 0, sizeof(double) * npoints * 27 * B * B);
   for (long t = 0; t < npoints; ++t) {
     long P = points[t];
@@ -683,17 +706,31 @@ typedef struct {
 
 /* Coarsening schedule: halve every dimension while all of them are even and
  * the smallest is at least 8 (fixed stride-2 full coarsening, Sec. 4.1 P2). */
-int orc_plan_levels(const int d[3], int max_levels, int dims_out[][3]) {
+/* The same for a transfer: with the x-y semi-coarsening of transfer 3 only
+ * x and y are halved, while both are even and the smaller is at least 8. */
+int orc_plan_levels_t(int transfer, const int d[3], int max_levels, int dims_out[][3]) {
   int c[3] = {d[0], d[1], d[2]};
+  const int nd = transfer == 3 ? 2 : 3;
   int L = 0;
   for (;;) {
     dims_out[L][0] = c[0]; dims_out[L][1] = c[1]; dims_out[L][2] = c[2];
     ++L;
-    int mn = c[0] < c[1] ? (c[0] < c[2] ? c[0] : c[2]) : (c[1] < c[2] ? c[1] : c[2]);
-    if (L >= max_levels || mn < 8 || (c[0] % 2) || (c[1] % 2) || (c[2] % 2)) break;
-    c[0] /= 2; c[1] /= 2; c[2] /= 2;
+    int mn = c[0];
+    int odd = 0;
+    for (int t = 0; t < nd; ++t) {
+      if (c[t] < mn) mn = c[t];
+      odd |= c[t] % 2;
+    }
+    if (L >= max_levels || mn < 8 || odd) break;
+    int cn[3];
+    orc_coarse_dims_t(transfer, c, cn);
+    c[0] = cn[0]; c[1] = cn[1]; c[2] = cn[2];
   }
   return L;
+}
+
+int orc_plan_levels(const int d[3], int max_levels, int dims_out[][3]) {
+  return orc_plan_levels_t(0, d, max_levels, dims_out);
 }
 
 static void level_free(orc_level* L) {
@@ -719,7 +756,7 @@ int orc_mg_setup(void** out, const int d[3], int ns, const int* off, int B, cons
   *out = NULL;
   if (orc_mask_validate(ns, off)) return ORC_EINVAL;
   if (B != 1 && B != 3) return ORC_EINVAL;
-  if (transfer < 0 || transfer > 2) return ORC_EINVAL;
+  if (transfer < 0 || transfer > 3) return ORC_EINVAL;
   if (B == 3 && smoother != SM_SGS) return ORC_EINVAL;
   if (smoother < SM_SGS || smoother > SM_LGS) return ORC_EINVAL;
   if (smoother == SM_LGS && (precision != 0 || w != 1.0)) return ORC_EINVAL;
@@ -729,7 +766,7 @@ int orc_mg_setup(void** out, const int d[3], int ns, const int* off, int B, cons
   orc_mg* mg = (orc_mg*)calloc(1, sizeof(orc_mg));
   mg->B = B; mg->smoother = smoother; mg->transfer = transfer; mg->w = w; mg->precision = precision;
   int dims[16][3];
-  mg->nlev = orc_plan_levels(d, max_levels < 16 ? max_levels : 16, dims);
+  mg->nlev = orc_plan_levels_t(transfer, d, max_levels < 16 ? max_levels : 16, dims);
   int rc = ORC_OK;
   for (int l = 0; l < mg->nlev; ++l) {
     orc_level* L = &mg->lev[l];
@@ -981,16 +1018,16 @@ static void ilu32(const orc_level* L, const float* r, float* x) {
 
 static void restrict32(int transfer, const int fd[3], const float* rf, float* fc) {
   int cd[3];
-  orc_coarse_dims(fd, cd);
+  orc_coarse_dims_t(transfer, fd, cd);
   for (int I0 = 0; I0 < cd[0]; ++I0)
     for (int I1 = 0; I1 < cd[1]; ++I1)
       for (int I2 = 0; I2 < cd[2]; ++I2) {
-        int I[3] = {I0, I1, I2}, base[3], span;
-        support(transfer, I, base, &span);
+        int I[3] = {I0, I1, I2}, base[3], span[3];
+        support(transfer, I, base, span);
         float s = 0.0f;
-        for (int a = 0; a < span; ++a)
-          for (int b = 0; b < span; ++b)
-            for (int c = 0; c < span; ++c) {
+        for (int a = 0; a < span[0]; ++a)
+          for (int b = 0; b < span[1]; ++b)
+            for (int c = 0; c < span[2]; ++c) {
               int u[3] = {base[0] + a, base[1] + b, base[2] + c};
               if (!inside(fd, u[0], u[1], u[2])) continue;
               s += (float)rweight(transfer, I, u) * rf[pidx(fd, u[0], u[1], u[2])];
@@ -1001,7 +1038,7 @@ static void restrict32(int transfer, const int fd[3], const float* rf, float* fc
 
 static void prolong32(int transfer, const int fd[3], const float* ec, float* uf) {
   int cd[3];
-  orc_coarse_dims(fd, cd);
+  orc_coarse_dims_t(transfer, fd, cd);
   for (int v0 = 0; v0 < fd[0]; ++v0)
     for (int v1 = 0; v1 < fd[1]; ++v1)
       for (int v2 = 0; v2 < fd[2]; ++v2) {
@@ -1010,7 +1047,8 @@ static void prolong32(int transfer, const int fd[3], const float* ec, float* uf)
         for (int a = -1; a <= 1; ++a)
           for (int b = -1; b <= 1; ++b)
             for (int c = -1; c <= 1; ++c) {
-              int J[3] = {v0 / 2 + a, v1 / 2 + b, v2 / 2 + c};
+              int J[3] = {coarse_of(transfer, 0, v0) + a, coarse_of(transfer, 1, v1) + b,
+                          coarse_of(transfer, 2, v2) + c};
               if (!inside(cd, J[0], J[1], J[2])) continue;
               double wgt = pweight(transfer, v, J);
               if (wgt == 0.0) continue;

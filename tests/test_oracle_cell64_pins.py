@@ -188,4 +188,4 @@ def test_cell64_hierarchy_solves_with_flexible_and_gmres(orc):
 def test_cell64_mg_rejects_unknown_transfer(orc):
     d = (8, 8, 8)
     with pytest.raises(Exception):
-        orc.MG(d, I.OFF7, I.laplace7(d).numpy(), transfer=3)
+        orc.MG(d, I.OFF7, I.laplace7(d).numpy(), transfer=4)
