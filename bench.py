@@ -74,6 +74,10 @@ WORKLOADS = {
                precision=0, krylov=0, tol=1e-9),
     "c7_128": dict(desc="zaniso27_128^3_lgs_fw27v_pcg_fp64", dims=(128, 128, 128), gen="q1z", smoother=2,
                    transfer=0, precision=0, krylov=0, tol=1e-9),
+    # the same matrix with 2-D semi-coarsening in x and y (2d4c / 2d16c) and
+    # z-line smoothing under FGMRES(30): Table 8's weather setting
+    "c8": dict(desc="zaniso27_256^3_lgs_semicoarse_xy_fgmres30_fp64", dims=(256, 256, 256), gen="q1z", smoother=2,
+               transfer=3, precision=0, krylov=2, tol=1e-9),
 }
 DEFAULT = "c2"
 HBM_PEAK_FALLBACK = 6800.0
@@ -451,7 +455,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     metric = "time to solution (set-up + Krylov to rel-res %g), %s" % (w["tol"], w["desc"])
     config = {"workload": w["desc"], "dims": list(w["dims"]), "unknowns_per_point": w.get("block", 1),
-              "smoother": ["sym-GS", "ILU(0)", "sym-LGS (z-lines)"][w["smoother"]], "transfer": ["3d27v", "3d8c", "3d64c interp. + 3d8c restr."][w["transfer"]],
+              "smoother": ["sym-GS", "ILU(0)", "sym-LGS (z-lines)"][w["smoother"]], "transfer": ["3d27v", "3d8c", "3d64c interp. + 3d8c restr.",
+                                                                "x-y semi-coarsening, 2d16c interp. + 2d4c restr."][w["transfer"]],
               "hierarchy_precision": ["fp64", "fp32", "bf16-rowscaled"][w["precision"]],
               "krylov": ["PCG", "FPCG", "FGMRES(30)"][w["krylov"]], "tol": w["tol"],
               "parallelism": "replicas" if args.gpus > 1 else "single-gpu",

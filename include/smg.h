@@ -49,7 +49,7 @@ typedef enum {
 } smg_status;
 
 enum { SMG_SMOOTHER_SGS = 0, SMG_SMOOTHER_ILU0 = 1, SMG_SMOOTHER_LGS = 2 };
-enum { SMG_TRANSFER_FW27V = 0, SMG_TRANSFER_PC8C = 1, SMG_TRANSFER_C64C = 2 };
+enum { SMG_TRANSFER_FW27V = 0, SMG_TRANSFER_PC8C = 1, SMG_TRANSFER_C64C = 2, SMG_TRANSFER_C16C_XY = 3 };
 enum { SMG_PREC_FP64 = 0, SMG_PREC_FP32 = 1, SMG_PREC_BF16 = 2 };
 enum { SMG_KRYLOV_PCG = 0, SMG_KRYLOV_FPCG = 1, SMG_KRYLOV_FGMRES = 2 };
 
@@ -78,7 +78,13 @@ enum { SMG_KRYLOV_PCG = 0, SMG_KRYLOV_FPCG = 1, SMG_KRYLOV_FGMRES = 2 };
  *                    settings of rhd-3T and solid-3D).  R is not a multiple
  *                    of P^T, so the coarse operators and the V-cycle are
  *                    nonsymmetric: use FPCG or FGMRES (PCG is accepted; the
- *                    paper runs CG with it).
+ *                    paper runs CG with it).  C16C_XY: 2-D semi-coarsening
+ *                    (Table 8, weather): only x and y are halved, z is
+ *                    kept; the 2 x 2 cell sum restricts and the cell-centred
+ *                    bilinear interpolation of C64C acts in x and y (2d4c /
+ *                    2d16c), so coarse grids keep whole z-columns for the
+ *                    LGS smoother.  Coarsening stops when x or y is odd or
+ *                    the smaller of them is below 8.
  *  precision  [FP64] storage and arithmetic of the hierarchy and V-cycle:
  *                    FP64, FP32, or BF16 values with one FP32 scale per row
  *                    and FP32 accumulation (not in the paper).  The Krylov

@@ -19,6 +19,14 @@ namespace smg_host {
 
 int derive_chains(int dim, int nr, const int* roff, int na, const int* aoff, int np, const int* poff,
                   std::vector<Chain>& out) {
+  const int stride[3] = {2, 2, 2};
+  return derive_chains_strided(dim, stride, nr, roff, na, aoff, np, poff, out);
+}
+
+// The same with a coarsening stride of 2 or 1 per dimension: a dimension
+// that is not coarsened (stride 1) maps fine offsets to coarse ones as is.
+int derive_chains_strided(int dim, const int* stride, int nr, const int* roff, int na, const int* aoff, int np,
+                          const int* poff, std::vector<Chain>& out) {
   out.clear();
   if (dim != 2 && dim != 3) return -1;
   for (int r = 0; r < nr; ++r)
@@ -28,6 +36,10 @@ int derive_chains(int dim, int nr, const int* roff, int na, const int* aoff, int
         bool ok = true;
         for (int t = 0; t < dim; ++t) {
           int d = roff[3 * r + t] + aoff[3 * a + t] - poff[3 * q + t];
+          if (stride[t] == 1) {
+            dj[t] = d;
+            continue;
+          }
           if (d & 1) { ok = false; break; }
           dj[t] = d / 2;
         }
@@ -67,6 +79,12 @@ int build_rap_table(int transfer, int ns_f, const int (*off_f)[3], RapTable& T) 
   } else if (transfer == SMG_TRANSFER_C64C) {
     cube(0, 1, rp);
     cube(-1, 2, pp);
+  } else if (transfer == SMG_TRANSFER_C16C_XY) {
+    // x and y as C64C, z not coarsened: every pattern has z offset 0
+    for (int a = 0; a <= 1; ++a)
+      for (int b = 0; b <= 1; ++b) rp.insert(rp.end(), {a, b, 0});
+    for (int a = -1; a <= 2; ++a)
+      for (int b = -1; b <= 2; ++b) pp.insert(pp.end(), {a, b, 0});
   } else {
     return -1;
   }
@@ -74,7 +92,9 @@ int build_rap_table(int transfer, int ns_f, const int (*off_f)[3], RapTable& T) 
   for (int e = 0; e < ns_f; ++e)
     for (int t = 0; t < 3; ++t) af[3 * e + t] = off_f[e][t];
   std::vector<Chain> ch;
-  int n = derive_chains(3, (int)rp.size() / 3, rp.data(), ns_f, af.data(), (int)pp.size() / 3, pp.data(), ch);
+  const int stride[3] = {2, 2, transfer == SMG_TRANSFER_C16C_XY ? 1 : 2};
+  int n = derive_chains_strided(3, stride, (int)rp.size() / 3, rp.data(), ns_f, af.data(), (int)pp.size() / 3,
+                                pp.data(), ch);
   if (n < 0) return -1;
   bool present[27] = {false};
   for (const Chain& c : ch) present[c.dj] = true;
@@ -105,6 +125,8 @@ int build_rap_table(int transfer, int ns_f, const int (*off_f)[3], RapTable& T) 
         wp = w1(po[0]) * w1(po[1]) * w1(po[2]);
       } else if (transfer == SMG_TRANSFER_C64C) {
         wp = wc(po[0]) * wc(po[1]) * wc(po[2]);
+      } else if (transfer == SMG_TRANSFER_C16C_XY) {
+        wp = wc(po[0]) * wc(po[1]);
       }
       RapEntry en;
       en.rx = ro[0]; en.ry = ro[1]; en.rz = ro[2];

@@ -25,6 +25,8 @@ struct RapTable {
 
 int derive_chains(int dim, int nr, const int* roff, int na, const int* aoff, int np, const int* poff,
                   std::vector<Chain>& out);
+int derive_chains_strided(int dim, const int* stride, int nr, const int* roff, int na, const int* aoff, int np,
+                          const int* poff, std::vector<Chain>& out);
 int build_rap_table(int transfer, int ns_f, const int (*off_f)[3], RapTable& T);
 void build_ilu_updates(int ns, const int (*off)[3], int ec, std::vector<int>& kstart, std::vector<int>& pairs);
 void schedule_skews(int ns, const int (*off)[3], int* SA, int* SB);

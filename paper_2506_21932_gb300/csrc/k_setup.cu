@@ -13,7 +13,7 @@ constexpr int TPB = 256;
 // Threads are numbered entry-major (idx = c * n_coarse + P) so the 32 lanes
 // of a warp share the coarse entry c and walk the same chain list.
 template <int B>
-__global__ void __launch_bounds__(TPB) k_rap(Grid f, Grid c, Stencil sc, int nsf, int ashift,
+__global__ void __launch_bounds__(TPB) k_rap(Grid f, Grid c, Stencil sc, int nsf, int ashift, int zs,
                                              const int* __restrict__ cstart, const int4* __restrict__ ent,
                                              const double* __restrict__ wt, const double* __restrict__ Af,
                                              double* __restrict__ Ac) {
@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(TPB) k_rap(Grid f, Grid c, Stencil sc, int nsf
   const bool jin = (unsigned)(I + sc.off[ce][0]) < (unsigned)c.nx && (unsigned)(J + sc.off[ce][1]) < (unsigned)c.ny &&
                    (unsigned)(K + sc.off[ce][2]) < (unsigned)c.nz;
   if (jin) {
-    const int u0 = 2 * I + ashift, u1 = 2 * J + ashift, u2 = 2 * K + ashift;
+    const int u0 = 2 * I + ashift, u1 = 2 * J + ashift, u2 = zs * K + ashift;
     for (int t = cstart[ce]; t < cstart[ce + 1]; ++t) {
       const int4 e = ent[t];
       const int a = u0 + e.x, b = u1 + e.y, cc = u2 + e.z;
@@ -54,12 +54,13 @@ cudaError_t launch_rap(int transfer, Grid fine, const Stencil& sf, int B, const 
                        const Stencil& sc, const int* cstart, const int4* chains, const double* weights, double* Ac,
                        cudaStream_t st) {
   const int ashift = transfer == SMG_TRANSFER_FW27V ? 1 : 0;
+  const int zs = transfer == SMG_TRANSFER_C16C_XY ? 1 : 2;  // z stride between coarse and fine
   const long long total = coarse.n * sc.ns;
   const int nb = div_up(total, TPB);
   if (B == 1)
-    k_rap<1><<<nb, TPB, 0, st>>>(fine, coarse, sc, sf.ns, ashift, cstart, chains, weights, Af, Ac);
+    k_rap<1><<<nb, TPB, 0, st>>>(fine, coarse, sc, sf.ns, ashift, zs, cstart, chains, weights, Af, Ac);
   else
-    k_rap<3><<<nb, TPB, 0, st>>>(fine, coarse, sc, sf.ns, ashift, cstart, chains, weights, Af, Ac);
+    k_rap<3><<<nb, TPB, 0, st>>>(fine, coarse, sc, sf.ns, ashift, zs, cstart, chains, weights, Af, Ac);
   smg_count_launch(1);
   return cudaGetLastError();
 }

@@ -1,5 +1,6 @@
 // Point-parallel stencil kernels: SG-DIA SpMV / residual (Sec. 6.1.1), grid
-// transfers (Sec. 2 V-cycle; Table 3 patterns 3d27v, 3d8c and 3d64c), precision
+// transfers (Sec. 2 V-cycle; Table 3 patterns 3d27v, 3d8c and 3d64c, and the
+// 2d4c / 2d16c pair of x-y semi-coarsening), precision
 // casts and lowering, diagonal inverses and the dense coarsest level.
 #include "smg_internal.cuh"
 
@@ -251,6 +252,69 @@ __global__ void __launch_bounds__(TPB) k_prolong_c64(Grid f, Grid c, const V* __
 #pragma unroll
         for (int r = 0; r < B; ++r) acc[r] = fma(wgt, ec[P * B + r], acc[r]);
       }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < B; ++r) uf[q * B + r] += acc[r];
+}
+
+// x-y semi-coarsening (2d4c / 2d16c): fc(I,J,K) = sum of the 2 x 2 fine
+// cells (2I + a, 2J + b, K); uf += P ec with the cell-centred bilinear
+// weights of k_prolong_c64 in x and y and the same z.
+template <typename V, int B>
+__global__ void __launch_bounds__(TPB) k_restrict_xy(Grid f, Grid c, const V* __restrict__ rf, V* __restrict__ fc) {
+  long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (P >= c.n) return;
+  int I, J, K;
+  coords(P, c, I, J, K);
+  V acc[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) acc[r] = 0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const long long q = ((long long)(2 * I + a) * f.ny + (2 * J + b)) * f.nz + K;
+#pragma unroll
+      for (int r = 0; r < B; ++r) acc[r] += rf[q * B + r];
+    }
+#pragma unroll
+  for (int r = 0; r < B; ++r) fc[P * B + r] = acc[r];
+}
+
+template <typename V, int B>
+__global__ void __launch_bounds__(TPB) k_prolong_xy(Grid f, Grid c, const V* __restrict__ ec, V* __restrict__ uf) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= f.n) return;
+  int v0, v1, v2;
+  coords(q, f, v0, v1, v2);
+  const int v[2] = {v0, v1};
+  const int cn[2] = {c.nx, c.ny};
+  int lo[2];
+  V w[2][2];
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    if (v[d] & 1) {
+      lo[d] = v[d] >> 1; w[d][0] = V(0.75); w[d][1] = V(0.25);
+    } else {
+      lo[d] = (v[d] >> 1) - 1; w[d][0] = V(0.25); w[d][1] = V(0.75);
+    }
+  }
+  V acc[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) acc[r] = 0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int J0 = lo[0] + a;
+    if ((unsigned)J0 >= (unsigned)cn[0]) continue;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int J1 = lo[1] + b;
+      if ((unsigned)J1 >= (unsigned)cn[1]) continue;
+      const V wgt = w[0][a] * w[1][b];
+      const long long P = ((long long)J0 * c.ny + J1) * c.nz + v2;
+#pragma unroll
+      for (int r = 0; r < B; ++r) acc[r] = fma(wgt, ec[P * B + r], acc[r]);
     }
   }
 #pragma unroll
@@ -522,19 +586,21 @@ cudaError_t launch_spmv(const LevelView& L, const void* x, const void* b, void* 
   return cudaGetLastError();
 }
 
-static Grid coarse_of(Grid f) {
-  Grid c{f.nx / 2, f.ny / 2, f.nz / 2, 0};
+static Grid coarse_of(Grid f, int transfer) {
+  Grid c{f.nx / 2, f.ny / 2, transfer == SMG_TRANSFER_C16C_XY ? f.nz : f.nz / 2, 0};
   c.n = (long long)c.nx * c.ny * c.nz;
   return c;
 }
 
 cudaError_t launch_restrict(int transfer, Grid f, int B, int pk, const void* rf, void* fc, cudaStream_t st) {
-  Grid c = coarse_of(f);
+  Grid c = coarse_of(f, transfer);
   int nb = div_up(c.n, TPB);
   bool dbl = pk == K64;
 #define RCASE(V, BB)                                                                                   \
   if (transfer == SMG_TRANSFER_FW27V)                                                                  \
     k_restrict_fw<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)rf, (V*)fc);                              \
+  else if (transfer == SMG_TRANSFER_C16C_XY)                                                           \
+    k_restrict_xy<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)rf, (V*)fc);                              \
   else                                                                                                 \
     k_restrict_pc<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)rf, (V*)fc);
   if (dbl) {
@@ -548,7 +614,7 @@ cudaError_t launch_restrict(int transfer, Grid f, int B, int pk, const void* rf,
 }
 
 cudaError_t launch_prolong_add(int transfer, Grid f, int B, int pk, const void* ec, void* uf, cudaStream_t st) {
-  Grid c = coarse_of(f);
+  Grid c = coarse_of(f, transfer);
   int nb = div_up(f.n, TPB);
   bool dbl = pk == K64;
 #define PCASE(V, BB)                                                                                   \
@@ -556,6 +622,8 @@ cudaError_t launch_prolong_add(int transfer, Grid f, int B, int pk, const void* 
     k_prolong_fw<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)ec, (V*)uf);                               \
   else if (transfer == SMG_TRANSFER_C64C)                                                              \
     k_prolong_c64<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)ec, (V*)uf);                              \
+  else if (transfer == SMG_TRANSFER_C16C_XY)                                                           \
+    k_prolong_xy<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)ec, (V*)uf);                               \
   else                                                                                                 \
     k_prolong_pc<V, BB><<<nb, TPB, 0, st>>>(f, c, (const V*)ec, (V*)uf);
   if (dbl) {

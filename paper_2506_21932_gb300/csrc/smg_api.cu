@@ -384,7 +384,11 @@ static int validate_mask(int ns, const int* off) {
   return SMG_OK;
 }
 
-static int plan_levels(const int d[3], int maxl, int dims[][3]) {
+// Coarsening schedule: halve every dimension while all are even and the
+// smallest is at least 8 (full coarsening), or only x and y under the same
+// rule for the x-y semi-coarsening transfer.
+static int plan_levels(const int d[3], int maxl, int transfer, int dims[][3]) {
+  const bool semi = transfer == SMG_TRANSFER_C16C_XY;
   int c[3] = {d[0], d[1], d[2]};
   int L = 0;
   for (;;) {
@@ -392,11 +396,12 @@ static int plan_levels(const int d[3], int maxl, int dims[][3]) {
     dims[L][1] = c[1];
     dims[L][2] = c[2];
     ++L;
-    int mn = std::min(c[0], std::min(c[1], c[2]));
-    if (L >= maxl || mn < 8 || (c[0] & 1) || (c[1] & 1) || (c[2] & 1)) break;
+    const int mn = semi ? std::min(c[0], c[1]) : std::min(c[0], std::min(c[1], c[2]));
+    const bool odd = (c[0] & 1) || (c[1] & 1) || (!semi && (c[2] & 1));
+    if (L >= maxl || mn < 8 || odd) break;
     c[0] /= 2;
     c[1] /= 2;
-    c[2] /= 2;
+    if (!semi) c[2] /= 2;
   }
   return L;
 }
@@ -504,8 +509,9 @@ static void compute_stats(smg_ctx* h) {
     }
     bpt += ns * c * bb + 3 * v * B + s;                                   // residual before restriction
     fpt += 2 * ns * bb;
-    bpt += v * B + v * B / 8.0;                                           // restriction
-    bpt += 2 * v * B + v * B / 8.0;                                       // prolongation + correction
+    const double cf = (double)h->L[l + 1].g.n / n;                        // coarse / fine points
+    bpt += v * B + v * B * cf;                                            // restriction
+    bpt += 2 * v * B + v * B * cf;                                        // prolongation + correction
     fpt += 2 * 27.0 / 8.0 * B * 2;
     bytes += bpt * n;
     flops += fpt * n;
@@ -525,7 +531,7 @@ static int do_setup(smg_ctx* h, const int dims[3], int ns, const int* offsets, c
   const int B = h->B;
   int pd[SMG_MAX_LEVELS][3];
   const int maxl = h->opt.max_levels > 0 ? std::min(h->opt.max_levels, SMG_MAX_LEVELS) : SMG_MAX_LEVELS;
-  h->nlev = plan_levels(dims, maxl, pd);
+  h->nlev = plan_levels(dims, maxl, h->opt.transfer, pd);
   TRY(dalloc(h, &h->err, 4));
   SMG_CUDA_TRY(cudaMemsetAsync(h->err, 0, 4 * sizeof(int), st));
   SMG_CUDA_TRY(cudaMallocHost(&h->hsc, SC_COUNT * sizeof(double)));
@@ -651,7 +657,7 @@ extern "C" int smg_setup(smg_t* out, const int dims[3], int nstencil, const int*
   TRY(validate_mask(nstencil, offsets));
   smg_options o{};
   if (opt) o = *opt;
-  if (o.smoother < 0 || o.smoother > 2 || o.transfer < 0 || o.transfer > 2 || o.precision < 0 || o.precision > 2 ||
+  if (o.smoother < 0 || o.smoother > 2 || o.transfer < 0 || o.transfer > 3 || o.precision < 0 || o.precision > 2 ||
       o.krylov < 0 || o.krylov > 2)
     return SMG_EINVAL;
   if (o.restart == 0) o.restart = 30;

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libsmg.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENOTCONV, ENAN, ETIMEOUT = range(8)
 SGS, ILU0, LGS = 0, 1, 2
-FW27V, PC8C, C64C = 0, 1, 2
+FW27V, PC8C, C64C, C16XY = 0, 1, 2, 3
 FP64, FP32, BF16 = 0, 1, 2
 PCG, FPCG, FGMRES = 0, 1, 2
 OP_SPMV, OP_RESIDUAL, OP_GS_FORWARD, OP_GS_BACKWARD, OP_GS_ZERO, OP_ILU_APPLY, OP_RESTRICT, OP_PROLONG_ADD, \

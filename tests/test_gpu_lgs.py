@@ -92,7 +92,8 @@ def test_line_sweeps_match_oracle(S, orc, d, kind):
 
 
 @pytest.mark.parametrize("d,kind,transfer", [((32, 32, 32), "q1z", 0), ((16, 24, 40), "fv", 0),
-                                             ((24, 16, 32), "q1", 2), ((16, 16, 16), "lap", 1)])
+                                             ((24, 16, 32), "q1", 2), ((16, 16, 16), "lap", 1),
+                                             ((32, 32, 24), "q1z", 3), ((16, 32, 45), "q1z19", 3)])
 def test_lgs_vcycle_matches_oracle(S, orc, d, kind, transfer):
     off, A = problem(kind, d)
     h = S.SMG(d, off, cu(A), smoother=S.LGS, transfer=transfer)
@@ -120,6 +121,28 @@ def test_lgs_pcg_solve_matches_oracle(S, orc):
     x.zero_()
     its, _, rcs = S.SMG(d, off, cu(A), smoother=S.SGS).solve(cu(b), x, tol=1e-9, maxit=500)
     assert rcs == 0 and its > 4 * it
+
+
+@pytest.mark.parametrize("krylov", [1, 2])
+def test_semicoarse_lgs_solve_matches_oracle(S, orc, krylov):
+    """x-y semi-coarsening with z-line smoothing (Table 8, weather setting)
+    under flexible PCG and FGMRES(30): iterations within one of the oracle's,
+    tolerance reached, true residual recomputed by the oracle."""
+    d = (32, 48, 40)
+    off, A = problem("q1z", d, seed=4)
+    b = I.rhs(int(np.prod(d)), 8).numpy()
+    x = torch.zeros_like(cu(b))
+    h = S.SMG(d, off, cu(A), smoother=S.LGS, transfer=S.C16XY, krylov=krylov, restart=30)
+    assert h.nlevels == 4 and h.level_info(3)[0] == (4, 6, 40)
+    it, rr, rc = h.solve(cu(b), x, tol=1e-9, maxit=300)
+    ref = orc.MG(d, off, A, smoother=orc.LGS, transfer=orc.C16XY)
+    if krylov == 2:
+        _, rcr, itr, _, _ = ref.fgmres(b, tol=1e-9, restart=30, maxit=300)
+    else:
+        _, rcr, itr, _, _ = ref.pcg(b, tol=1e-9, flexible=True, maxit=300)
+    assert rc == 0 and rcr == 0 and abs(it - itr) <= 1 and rr < 1e-9
+    res = np.linalg.norm(orc.residual(d, off, A, b, host(x))) / np.linalg.norm(b)
+    assert res < 1e-9
 
 
 def test_lgs_argument_checks_and_breakdown(S):

@@ -196,7 +196,9 @@ def test_ilu0_tridiagonal_exact_solve(S, orc):
     ((16, 12, 20), I.OFF7, 0, 1, "lap"), ((16, 16, 16), I.OFF27, 0, 1, "q1"), ((24, 16, 16), I.OFF27, 0, 1, "rnd"),
     ((16, 16, 8), I.OFF7, 1, 3, "blk"), ((16, 8, 24), I.OFF7, 1, 1, "rnd"),
     ((16, 12, 20), I.OFF7, 2, 1, "lap"), ((16, 16, 16), I.OFF27, 2, 1, "q1"), ((24, 16, 16), I.OFF19, 2, 1, "rnd"),
-    ((16, 16, 8), I.OFF7, 2, 3, "blk"), ((16, 8, 24), I.OFF7, 2, 1, "fv")])
+    ((16, 16, 8), I.OFF7, 2, 3, "blk"), ((16, 8, 24), I.OFF7, 2, 1, "fv"),
+    ((16, 24, 12), I.OFF7, 3, 1, "lap"), ((16, 16, 10), I.OFF27, 3, 1, "q1"), ((24, 16, 7), I.OFF19, 3, 1, "rnd"),
+    ((16, 16, 6), I.OFF7, 3, 3, "blk")])
 def test_galerkin_hierarchy(S, orc, d, off, transfer, B, gen):
     A = {"lap": lambda: I.laplace7(d).numpy(), "q1": lambda: I.q1_aniso27(d, 2).numpy(),
          "rnd": lambda: rnd_sym27(d, 5, off), "blk": lambda: I.block7_layered(d, 4).numpy(),
@@ -222,13 +224,15 @@ def test_galerkin_hierarchy(S, orc, d, off, transfer, B, gen):
         assert np.all(Ag.reshape(pad.shape)[pad] == 0.0)
 
 
-@pytest.mark.parametrize("transfer,B", [(0, 1), (1, 1), (2, 1), (0, 3), (1, 3), (2, 3)])
+@pytest.mark.parametrize("transfer,B", [(0, 1), (1, 1), (2, 1), (3, 1), (0, 3), (1, 3), (2, 3), (3, 3)])
 def test_restrict_prolong(S, orc, transfer, B):
     d = (10, 12, 8) if B == 1 else (8, 8, 10)
+    if transfer == 3:
+        d = (d[0], d[1], 7)  # z is not coarsened: any length
     A = I.laplace7(d).numpy() if B == 1 else I.block7_layered(d, 0).numpy()
     h = make(S, d, I.OFF7, A, block=B, transfer=transfer, max_levels=2)
     nf = np.prod(d) * B
-    nc = np.prod(orc.coarse_dims(d)) * B
+    nc = np.prod(orc.coarse_dims(d, transfer)) * B
     rf, ec, uf = np.random.default_rng(3).normal(size=(3, max(nf, nc)))
     rf, ec, uf = rf[:nf], ec[:nc], uf[:nf]
     y = torch.empty(nc, dtype=torch.float64, device="cuda")
@@ -245,7 +249,8 @@ def test_restrict_prolong(S, orc, transfer, B):
 
 VCASES = [((32, 32, 32), "lap", 0, 0, 1), ((24, 16, 32), "q1", 1, 0, 1), ((16, 24, 16), "q1", 0, 0, 1),
           ((16, 16, 16), "blk", 0, 1, 3), ((20, 16, 24), "q1", 1, 0, 1), ((32, 32, 32), "fv", 0, 2, 1),
-          ((24, 16, 32), "fv", 1, 2, 1), ((16, 24, 16), "q1", 1, 2, 1), ((16, 16, 16), "blk", 0, 2, 3)]
+          ((24, 16, 32), "fv", 1, 2, 1), ((16, 24, 16), "q1", 1, 2, 1), ((16, 16, 16), "blk", 0, 2, 3),
+          ((32, 32, 20), "fv", 0, 3, 1), ((16, 32, 24), "q1", 1, 3, 1), ((16, 16, 12), "blk", 0, 3, 3)]
 
 
 def problem(kind, d, seed=1):
