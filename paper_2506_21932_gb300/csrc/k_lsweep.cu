@@ -9,13 +9,15 @@
 // 7-point mask) of plane i - 1, progress published by the wavefront engine's
 // publisher / poller warps.
 //
-// A column is solved by one warp.  The serial Thomas recurrence of the
-// paper would put 2 nz dependent FP64 operations on the critical path, so
-// the column is cut into 32 chunks of m rows, one per lane (partition
-// method): every lane eliminates its rows 2..m in terms of its own first
-// unknown P_L and the next chunk's first unknown P_{L+1}, the 32 chunk-first
-// unknowns form a tridiagonal system solved by parallel cyclic reduction
-// across the lanes, and each lane then recovers its rows.  Everything that
+// A column is solved by four warps, one per SM sub-partition (each of which
+// issues about one FP64 warp instruction per 64 cycles on GB300).  The serial
+// Thomas recurrence of the paper would put 2 nz dependent FP64 operations on
+// the critical path, so the column is cut into 128 chunks of m rows, one per
+// thread (partition method): every thread eliminates its rows 2..m in terms
+// of its own first unknown P_c and the next chunk's first unknown P_{c+1},
+// the 128 chunk-first unknowns form a tridiagonal system solved by parallel
+// cyclic reduction through shared memory, and each thread then recovers its
+// rows.  Everything that
 // depends only on the matrix (reciprocal pivots, elimination multipliers,
 // the reduced system's PCR multipliers) is computed once at set-up, so a
 // sweep does no division.  In exact arithmetic the result is the Thomas
@@ -31,21 +33,27 @@ namespace {
 
 constexpr int kLgsWarps = 8;                       // compute warps of a CTA
 constexpr int kLgsThreads = (kLgsWarps + 2) * 32;  // + publisher + poller
-constexpr int kLgsMaxM = 32;                       // rows per chunk: nz <= 1024
-constexpr unsigned kFull = 0xffffffffu;
+constexpr int kLgsSolveWarps = 4;                  // warps solving a column (warps 0..3)
+constexpr int kLgsChunks = 32 * kLgsSolveWarps;      // chunks of a column, one per solving thread
+constexpr int kLgsPcr = 7;                           // PCR steps: log2(kLgsChunks)
+constexpr int kLgsMaxM = 8;                          // rows per chunk: nz <= 1024
 
-// Column block of the line factors, in doubles, every field 32 lanes wide:
+// Column block of the line factors, in doubles, every field kLgsChunks wide:
 // for chunk rows r = 1..m-1 the fields F_W (a_r / den_r), F_INV (1 / den_r),
-// F_CP (c_r / den_r), F_G, F_H (x_r = e_r - g_r P_{L+1} - h_r P_L); then per
+// F_CP (c_r / den_r), F_G, F_H (x_r = e_r - g_r P_{c+1} - h_r P_c); then per
 // chunk C_A0, C_C0 (the couplings of its first row), C_AL + t, C_GA + t (the
 // PCR multipliers of step t, stride 2^t) and C_INVB (1 / final pivot).
 enum { F_W, F_INV, F_CP, F_G, F_H, F_N };
-enum { C_A0 = 0, C_C0 = 1, C_AL = 2, C_GA = 7, C_INVB = 12, C_N = 13 };
-__host__ __device__ inline int lgs_row(int r, int f) { return ((r - 1) * F_N + f) * 32; }
-__host__ __device__ inline int lgs_chunk(int m, int f) { return ((m - 1) * F_N + f) * 32; }
+enum { C_A0 = 0, C_C0 = 1, C_AL = 2, C_GA = 2 + kLgsPcr, C_INVB = 2 + 2 * kLgsPcr, C_N = 3 + 2 * kLgsPcr };
+__host__ __device__ inline int lgs_row(int r, int f) { return ((r - 1) * F_N + f) * kLgsChunks; }
+__host__ __device__ inline int lgs_chunk(int m, int f) { return ((m - 1) * F_N + f) * kLgsChunks; }
 
 __device__ __forceinline__ void lgs_bar() {
   asm volatile("bar.sync 1, %0;" ::"n"(kLgsWarps * 32) : "memory");
+}
+// barrier of the solving warps only
+__device__ __forceinline__ void lgs_bar_solve() {
+  asm volatile("bar.sync 2, %0;" ::"n"(kLgsChunks) : "memory");
 }
 
 struct LineIdx {
@@ -84,66 +92,71 @@ __global__ void k_lgs_pivots(Grid g, int ns, LineIdx e, const double* __restrict
   }
 }
 
-// One warp per column, lane L = chunk L: the partitioned elimination of
-// rows L*m + 1 .. L*m + m-1 and the reduced system's PCR multipliers.
-__global__ void k_lgs_factor(Grid g, int ns, LineIdx e, const double* __restrict__ A, double* __restrict__ Fo, int m,
-                             long long blk, int* err) {
-  const long long col = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (col >= (long long)g.nx * g.ny) return;  // warp-uniform
-  const int L = threadIdx.x & 31;
+// One block of kLgsChunks threads per column, thread c = chunk c: the
+// partitioned elimination of rows c*m + 1 .. c*m + m-1 and the reduced
+// system's PCR multipliers (neighbour values through shared memory).
+__global__ void __launch_bounds__(kLgsChunks) k_lgs_factor(Grid g, int ns, LineIdx e, const double* __restrict__ A,
+                                                           double* __restrict__ Fo, int m, long long blk, int* err) {
+  __shared__ double xa[kLgsChunks], xb[kLgsChunks], xc[kLgsChunks];
+  const long long col = blockIdx.x;
+  const int c = threadIdx.x;
   double* F = Fo + col * blk;
   double cp[kLgsMaxM], fp[kLgsMaxM];
   bool bad = false;
   for (int r = 1; r < m; ++r) {
-    double a, b, c;
-    line_coef(g, ns, e, A, col, L * m + r, a, b, c);
+    double a, b, cc;
+    line_coef(g, ns, e, A, col, c * m + r, a, b, cc);
     const double den = r == 1 ? b : b - a * cp[r - 1];
     bad |= !(den > 0.0);
     const double inv = 1.0 / den;
-    cp[r] = c * inv;
+    cp[r] = cc * inv;
     fp[r] = (r == 1 ? a : -a * fp[r - 1]) * inv;
-    F[lgs_row(r, F_W) + L] = a * inv;
-    F[lgs_row(r, F_INV) + L] = inv;
-    F[lgs_row(r, F_CP) + L] = cp[r];
+    F[lgs_row(r, F_W) + c] = a * inv;
+    F[lgs_row(r, F_INV) + c] = inv;
+    F[lgs_row(r, F_CP) + c] = cp[r];
   }
   double gg = cp[m - 1], hh = fp[m - 1];
   const double glast = gg, hlast = hh;
-  F[lgs_row(m - 1, F_G) + L] = gg;
-  F[lgs_row(m - 1, F_H) + L] = hh;
+  F[lgs_row(m - 1, F_G) + c] = gg;
+  F[lgs_row(m - 1, F_H) + c] = hh;
   for (int r = m - 2; r >= 1; --r) {
     hh = fp[r] - cp[r] * hh;
     gg = -cp[r] * gg;
-    F[lgs_row(r, F_G) + L] = gg;
-    F[lgs_row(r, F_H) + L] = hh;
+    F[lgs_row(r, F_G) + c] = gg;
+    F[lgs_row(r, F_H) + c] = hh;
   }
-  // reduced row of chunk L in P_{L-1}, P_L, P_{L+1}
+  // reduced row of chunk c in P_{c-1}, P_c, P_{c+1}
   double a0, b0, c0;
-  line_coef(g, ns, e, A, col, L * m, a0, b0, c0);
-  double gl = __shfl_up_sync(kFull, glast, 1), hl = __shfl_up_sync(kFull, hlast, 1);
-  if (L == 0) gl = hl = 0.0;
+  line_coef(g, ns, e, A, col, c * m, a0, b0, c0);
+  xa[c] = glast;
+  xb[c] = hlast;
+  __syncthreads();
+  const double gl = c > 0 ? xa[c - 1] : 0.0, hl = c > 0 ? xb[c - 1] : 0.0;
   double Ar = -a0 * hl;
   double Br = b0 - a0 * gl - c0 * hh;  // hh, gg now hold h_1, g_1
   double Cr = -c0 * gg;
-  F[lgs_chunk(m, C_A0) + L] = a0;
-  F[lgs_chunk(m, C_C0) + L] = c0;
-#pragma unroll
-  for (int t = 0; t < 5; ++t) {
+  F[lgs_chunk(m, C_A0) + c] = a0;
+  F[lgs_chunk(m, C_C0) + c] = c0;
+  for (int t = 0; t < kLgsPcr; ++t) {
     const int s = 1 << t;
-    const double Am = __shfl_up_sync(kFull, Ar, s), Bm = __shfl_up_sync(kFull, Br, s),
-                 Cm = __shfl_up_sync(kFull, Cr, s);
-    const double Ap = __shfl_down_sync(kFull, Ar, s), Bp = __shfl_down_sync(kFull, Br, s),
-                 Cp = __shfl_down_sync(kFull, Cr, s);
-    const bool lo = L >= s, hi = L + s < 32;
+    __syncthreads();
+    xa[c] = Ar;
+    xb[c] = Br;
+    xc[c] = Cr;
+    __syncthreads();
+    const bool lo = c >= s, hi = c + s < kLgsChunks;
+    const double Am = lo ? xa[c - s] : 0.0, Bm = lo ? xb[c - s] : 1.0, Cm = lo ? xc[c - s] : 0.0;
+    const double Ap = hi ? xa[c + s] : 0.0, Bp = hi ? xb[c + s] : 1.0, Cp = hi ? xc[c + s] : 0.0;
     const double al = lo ? -Ar / Bm : 0.0, ga = hi ? -Cr / Bp : 0.0;
-    const double nB = Br + (lo ? al * Cm : 0.0) + (hi ? ga * Ap : 0.0);
-    Ar = lo ? al * Am : 0.0;
-    Cr = hi ? ga * Cp : 0.0;
+    const double nB = Br + al * Cm + ga * Ap;
+    Ar = al * Am;
+    Cr = ga * Cp;
     Br = nB;
-    F[lgs_chunk(m, C_AL + t) + L] = al;
-    F[lgs_chunk(m, C_GA + t) + L] = ga;
+    F[lgs_chunk(m, C_AL + t) + c] = al;
+    F[lgs_chunk(m, C_GA + t) + c] = ga;
   }
   bad |= !(Br > 0.0);
-  F[lgs_chunk(m, C_INVB) + L] = 1.0 / Br;
+  F[lgs_chunk(m, C_INVB) + c] = 1.0 / Br;
   if (bad) atomicCAS(err, 0, SMG_EBREAKDOWN);
 }
 
@@ -178,7 +191,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // column factors, and with STAGE two buffers of the column's matrix rows
 // [nz][ns] and right-hand side [nz].
 __host__ __device__ inline long long lgs_smem_doubles(int m, long long blk, int nz, int ns, bool stage) {
-  return 2LL * 32 * (m + 1) + 2 * blk + (stage ? 2LL * ((long long)nz * ns + nz) : 0);
+  return 2LL * kLgsChunks * (m + 1) + kLgsChunks + 2 * blk + (stage ? 2LL * ((long long)nz * ns + nz) : 0);
 }
 
 // One off-column term of a point's right-hand side for a canonical mask
@@ -219,16 +232,15 @@ __device__ __forceinline__ void line_terms(double (&acc)[4], const double* __res
   (line_term<NS, KIND, DIR, Es>(acc, arow, up, xs, kc, kr, m, mp, lin, xymask, zmask), ...);
 }
 
-// STAGE: the next column's matrix rows and right-hand side are copied to
-// shared memory while the current one is solved (needs even nz, 16-byte
-// aligned A and b, and room); otherwise they are read from global memory.
-// Forward and backward elimination of rows 1..m-1 of lane L's chunk, the
-// PCR solve of the chunk-first unknowns and the recovery of the rows: x (in
-// the chunk layout) from the right-hand side d (overwritten).  The loads of
-// each group of four rows are issued before the dependent arithmetic.
+// Forward and backward elimination of rows 1..m-1 of chunk c, the PCR
+// solve of the chunk-first unknowns (through xch, kLgsChunks doubles) and
+// the recovery of the rows: x (in the chunk layout) from the right-hand side
+// d (overwritten).  Called by the kLgsChunks threads of the solving warps.
+// (xch is written and read by different threads between barriers, so it
+// carries no __restrict__: its loads must not move across the barriers.)
 __device__ __forceinline__ void lgs_solve_column(double* __restrict__ d, double* __restrict__ x,
-                                                 const double* __restrict__ fc, int m, int L) {
-  const int mp = m + 1, base = L * mp;
+                                                 const double* __restrict__ fc, double* xch, int m, int c) {
+  const int mp = m + 1, base = c * mp;
   double v = 0.0;
   for (int r0 = 1; r0 < m; r0 += 4) {
     double dv[4], iv[4], wv[4];
@@ -237,8 +249,8 @@ __device__ __forceinline__ void lgs_solve_column(double* __restrict__ d, double*
       const int r = r0 + q;
       if (r < m) {
         dv[q] = d[base + r];
-        iv[q] = fc[lgs_row(r, F_INV) + L];
-        wv[q] = fc[lgs_row(r, F_W) + L];
+        iv[q] = fc[lgs_row(r, F_INV) + c];
+        wv[q] = fc[lgs_row(r, F_W) + c];
       }
     }
 #pragma unroll
@@ -259,7 +271,7 @@ __device__ __forceinline__ void lgs_solve_column(double* __restrict__ d, double*
       const int r = r0 - q;
       if (r >= 1) {
         dv[q] = d[base + r];
-        cv[q] = fc[lgs_row(r, F_CP) + L];
+        cv[q] = fc[lgs_row(r, F_CP) + c];
       }
     }
 #pragma unroll
@@ -271,24 +283,32 @@ __device__ __forceinline__ void lgs_solve_column(double* __restrict__ d, double*
       }
     }
   }
-  double al[5], ga[5];
+  double al[kLgsPcr], ga[kLgsPcr];
 #pragma unroll
-  for (int t = 0; t < 5; ++t) {
-    al[t] = fc[lgs_chunk(m, C_AL + t) + L];
-    ga[t] = fc[lgs_chunk(m, C_GA + t) + L];
+  for (int t = 0; t < kLgsPcr; ++t) {
+    al[t] = fc[lgs_chunk(m, C_AL + t) + c];
+    ga[t] = fc[lgs_chunk(m, C_GA + t) + c];
   }
-  const double a0 = fc[lgs_chunk(m, C_A0) + L], c0 = fc[lgs_chunk(m, C_C0) + L];
-  const double invb = fc[lgs_chunk(m, C_INVB) + L];
-  const double e1 = d[base + 1], elast = d[base + m - 1];
-  const double eprev = __shfl_up_sync(kFull, elast, 1);
-  double D = fma(-c0, e1, fma(-a0, L > 0 ? eprev : 0.0, d[base]));
+  const double a0 = fc[lgs_chunk(m, C_A0) + c], c0 = fc[lgs_chunk(m, C_C0) + c];
+  const double invb = fc[lgs_chunk(m, C_INVB) + c];
+  const double e1 = d[base + 1];
+  xch[c] = d[base + m - 1];  // e_{m-1}, read by the next chunk
+  lgs_bar_solve();
+  double D = fma(-c0, e1, fma(-a0, c > 0 ? xch[c - 1] : 0.0, d[base]));
 #pragma unroll
-  for (int t = 0; t < 5; ++t) {
-    const double Dm = __shfl_up_sync(kFull, D, 1 << t), Dp = __shfl_down_sync(kFull, D, 1 << t);
+  for (int t = 0; t < kLgsPcr; ++t) {
+    const int s = 1 << t;
+    lgs_bar_solve();  // every read of xch is done
+    xch[c] = D;
+    lgs_bar_solve();
+    const double Dm = c >= s ? xch[c - s] : 0.0, Dp = c + s < kLgsChunks ? xch[c + s] : 0.0;
     D = fma(al[t], Dm, fma(ga[t], Dp, D));
   }
   const double Pv = D * invb;
-  const double Pn = __shfl_down_sync(kFull, Pv, 1);
+  lgs_bar_solve();
+  xch[c] = Pv;
+  lgs_bar_solve();
+  const double Pn = c + 1 < kLgsChunks ? xch[c + 1] : 0.0;
   x[base] = Pv;
   for (int r0 = 1; r0 < m; r0 += 4) {
     double ev[4], gv[4], hv[4];
@@ -297,8 +317,8 @@ __device__ __forceinline__ void lgs_solve_column(double* __restrict__ d, double*
       const int r = r0 + q;
       if (r < m) {
         ev[q] = d[base + r];
-        gv[q] = fc[lgs_row(r, F_G) + L];
-        hv[q] = fc[lgs_row(r, F_H) + L];
+        gv[q] = fc[lgs_row(r, F_G) + c];
+        hv[q] = fc[lgs_row(r, F_H) + c];
       }
     }
 #pragma unroll
@@ -321,12 +341,13 @@ __global__ void __launch_bounds__(kLgsThreads, 1) k_lsweep(LsParams P) {
   extern __shared__ __align__(16) double lgs_sm[];
   const Grid g = P.g;
   const int ns = P.s.ns;
-  const int m = P.m, mp = m + 1, nzp = 32 * m;
+  const int m = P.m, mp = m + 1, nzp = kLgsChunks * m;
   const long long blk = P.blk, na = (long long)g.nz * ns;
-  // shared-memory offsets (doubles): rhs and x in the chunk layout, two
-  // factor buffers, with STAGE two buffers of matrix rows and of b
-  const int o_rhs = 0, o_x = 32 * mp;
-  const long long o_fac = 64LL * mp, o_a = o_fac + 2 * blk, o_b = o_a + 2 * na;
+  // shared-memory offsets (doubles): rhs and x in the chunk layout, the PCR
+  // exchange row, two factor buffers, with STAGE two buffers of matrix rows
+  // and of b
+  const int o_rhs = 0, o_x = kLgsChunks * mp, o_xch = 2 * kLgsChunks * mp;
+  const long long o_fac = o_xch + kLgsChunks, o_a = o_fac + 2 * blk, o_b = o_a + 2 * na;
   const double* __restrict__ A = P.A;
   const double* __restrict__ b = P.b;
   double* u = P.u;
@@ -417,7 +438,8 @@ __global__ void __launch_bounds__(kLgsThreads, 1) k_lsweep(LsParams P) {
             lgs_sm[o_rhs + kc * mp + kr] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
           }
           lgs_bar();
-          if (tid < 32) lgs_solve_column(lgs_sm + o_rhs, lgs_sm + o_x, lgs_sm + o_fac + sel * blk, m, lane);
+          if (tid < kLgsChunks)
+            lgs_solve_column(lgs_sm + o_rhs, lgs_sm + o_x, lgs_sm + o_fac + sel * blk, lgs_sm + o_xch, m, tid);
           lgs_bar();
           for (int k = tid; k < g.nz; k += kLgsWarps * 32) {
             const int kc = k / m;
@@ -477,11 +499,11 @@ cudaError_t launch_stage(bool stage, int kind, int dir, const LsParams& P, int g
 }  // namespace
 
 int lgs_chunk_rows(int nz) {
-  const int m = (nz + 31) / 32;
+  const int m = (nz + kLgsChunks - 1) / kLgsChunks;
   return m < 2 ? 2 : m;
 }
 
-long long lgs_block_doubles(int nz) { return (long long)((lgs_chunk_rows(nz) - 1) * F_N + C_N) * 32; }
+long long lgs_block_doubles(int nz) { return (long long)((lgs_chunk_rows(nz) - 1) * F_N + C_N) * kLgsChunks; }
 
 bool lgs_supported(const Grid& g, const Stencil& s) {
   const LineIdx e = line_idx(s);
@@ -496,8 +518,8 @@ cudaError_t launch_lgs_setup(const Grid& g, const Stencil& s, const double* A, d
   k_lgs_pivots<<<div_up(ncol, 128), 128, 0, st>>>(g, s.ns, e, A, err);
   cudaError_t r = cudaGetLastError();
   if (r != cudaSuccess) return r;
-  k_lgs_factor<<<div_up(ncol * 32, 128), 128, 0, st>>>(g, s.ns, e, A, F, lgs_chunk_rows(g.nz),
-                                                        lgs_block_doubles(g.nz), err);
+  k_lgs_factor<<<(unsigned)ncol, kLgsChunks, 0, st>>>(g, s.ns, e, A, F, lgs_chunk_rows(g.nz),
+                                                       lgs_block_doubles(g.nz), err);
   smg_count_launch(2);
   return cudaGetLastError();
 }
