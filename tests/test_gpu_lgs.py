@@ -166,3 +166,17 @@ def test_lgs_argument_checks_and_breakdown(S):
     with pytest.raises(S.SmgError):
         h.level_apply(0, S.OP_LGS_FORWARD, x=torch.zeros(1024, dtype=torch.float64, device="cuda"),
                       b=torch.zeros(1024, dtype=torch.float64, device="cuda"))
+
+
+def test_lgs_vcycle_graph_replay_and_determinism(S):
+    """The line sweeps replay inside a captured V-cycle graph and give the
+    same bits as the eager V-cycle, run after run."""
+    d = (32, 32, 40)
+    off, A = problem("q1z", d)
+    r = cu(I.rhs(int(np.prod(d)), 3).numpy())
+    z1, z2, z3 = (torch.empty_like(r) for _ in range(3))
+    S.SMG(d, off, cu(A), smoother=S.LGS).vcycle(r, z1)
+    hg = S.SMG(d, off, cu(A), smoother=S.LGS, use_graph=1)
+    hg.vcycle(r, z2)
+    hg.vcycle(r, z3)
+    assert torch.equal(z1, z2) and torch.equal(z2, z3)
