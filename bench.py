@@ -347,7 +347,7 @@ def run_ours(args, w, rank, world):
     # (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel on the
     # same problem at 128^3, scaled by the 8x points of a 256^3 launch; None
     # where no capture of the current kernel exists
-    traffic = {"c2": round(8 * (483.945728e6 + 17.004544e6))}.get(args.workload)
+    traffic = {"c2": round(8 * (483.681536e6 + 16.680960e6))}.get(args.workload)
     if fp64:
         roof = {"bound": "alu", "achieved": round(k_tf, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(k_tf / FP64_PEAK_TFLOPS, 4), "traffic": traffic, "kernel": kname,
