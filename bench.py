@@ -314,7 +314,12 @@ def run_ours(args, w, rank, world):
     kfile = ("k_sweep3" if ny <= 512 else "k_sweep2") if B == 1 else ("k_bsweep3" if ny <= 512 else "k_sweep (3x3 blocks)")
     if w["smoother"] == 2:
         op, kname = smg.OP_LGS_FORWARD, "k_lsweep (line Gauss-Seidel forward, level 0)"
-        flops_pt, bytes_pt = 2 * (nsf - 3) + 10, nsf * cbytes + 5 * 8 + 3 * vbytes
+        # column factors: 128 chunks of m rows, 5 doubles per chunk row after the
+        # first and 17 per chunk, per column of nz points
+        nz = int(w["dims"][2])
+        m = max(2, -(-nz // 128))
+        fac_pt = 8.0 * ((m - 1) * 5 + 17) * 128 / nz
+        flops_pt, bytes_pt = 2 * (nsf - 3) + 10, nsf * cbytes + fac_pt + 3 * vbytes
         vec.zero_()
         run_k = lambda: h.level_apply(0, op, x=vec, b=rhs)
     elif w["smoother"] == 1:
