@@ -494,8 +494,9 @@ static void compute_stats(smg_ctx* h) {
     // per point, each array touched once per kernel
     double bpt = 0, fpt = 0;
     if (h->opt.smoother == SMG_SMOOTHER_LGS) {
-      // four line sweeps: the matrix row, 5 line factors, b, u read + write
-      bpt += 4 * (ns * c + 5 * 8.0 + 3 * v);
+      // four line sweeps: the matrix row, the column factors, b, u read + write
+      const double fpt_bytes = 8.0 * (double)lgs_block_doubles(L.g.nz) / L.g.nz;
+      bpt += 4 * (ns * c + fpt_bytes + 3 * v);
       fpt += 4 * (2 * (ns - 3) + 10);
     } else if (h->opt.smoother == SMG_SMOOTHER_SGS) {
       bpt += nlow * c * bb + cd * bb + 2 * v * B + s;                    // GS_ZERO forward
