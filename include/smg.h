@@ -237,6 +237,14 @@ int smg_selftest_wait(smg_t h, int budget_ms, void* stream);
 int smg_derive_chains(int dim, int nr, const int* roff, int na, const int* aoff, int np, const int* poff,
                       int max_chains, int* chains);
 
+/* Host-only: the Galerkin chain table the hierarchy set-up uses for one
+ * transfer (SMG_TRANSFER_*) on a fine mask of nstencil offsets (int[3] each,
+ * any order).  Returns the number of chains (Table 3 counts them: 1216 for
+ * C64C on 19 points, 1728 on 27) and writes the coarse mask size to
+ * *ncoarse if it is not NULL; -1 for an unknown transfer or a mask the
+ * derivation rejects.  No GPU is used. */
+int smg_rap_chain_count(int transfer, int nstencil, const int* offsets, int* ncoarse);
+
 /* ---------------------------------------------------------------------------
  * Learned post-smoother (not in the paper).  A three-layer 3x3x3
  * convolutional network f (2 -> 16 -> 16 -> 1 channels, ReLU after the first

@@ -176,6 +176,17 @@ void schedule_skews(int ns, const int (*off)[3], int* SA, int* SB) {
 
 }  // namespace smg_host
 
+extern "C" int smg_rap_chain_count(int transfer, int nstencil, const int* offsets, int* ncoarse) {
+  if (nstencil < 1 || nstencil > 27 || !offsets) return -1;
+  int off[27][3];
+  for (int e = 0; e < nstencil; ++e)
+    for (int t = 0; t < 3; ++t) off[e][t] = offsets[3 * e + t];
+  smg_host::RapTable T;
+  const int n = smg_host::build_rap_table(transfer, nstencil, off, T);
+  if (n >= 0 && ncoarse) *ncoarse = T.ns_c;
+  return n;
+}
+
 extern "C" int smg_derive_chains(int dim, int nr, const int* roff, int na, const int* aoff, int np, const int* poff,
                                  int max_chains, int* chains) {
   if (nr < 0 || na < 0 || np < 0 || (nr && !roff) || (na && !aoff) || (np && !poff)) return -1;

@@ -66,6 +66,7 @@ def lib():
         L.smg_level_copy.argtypes = [vp, i, i, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), vp]
         L.smg_level_apply.argtypes = [vp, i, i, vp, vp, vp, vp]
         L.smg_derive_chains.argtypes = [i, i, ip, i, ip, i, ip, i, ip]
+        L.smg_rap_chain_count.argtypes = [i, i, ip, ip]
         L.smg_version.restype = ctypes.c_char_p
         L.smg_launch_count.restype = ctypes.c_longlong
         L.smg_selftest_wait.argtypes = [vp, i, vp]
@@ -156,6 +157,16 @@ def derive_chains(roff, aoff, poff, dim=3):
     buf = (ctypes.c_int * (5 * max(1, n)))()
     L.smg_derive_chains(dim, len(roff), ro, len(aoff), ao, len(poff), po, n, buf)
     return [tuple(buf[5 * t:5 * t + 4]) for t in range(n)]
+
+
+def rap_chain_count(transfer, offsets):
+    """Host-only: (chains, coarse mask size) of the set-up's Galerkin chain table."""
+    L = lib()
+    nc = ctypes.c_int(0)
+    n = L.smg_rap_chain_count(transfer, len(offsets), _iarr([c for o in offsets for c in o]), ctypes.byref(nc))
+    if n < 0:
+        raise ValueError("no chain table for this transfer / mask")
+    return n, nc.value
 
 
 def _stream(stream):

@@ -134,3 +134,23 @@ def test_setup_rejects_bad_arguments(smg):
     assert L.smg_vcycle(None, None, None, None) == smg.EINVAL
     assert L.smg_solve(None, None, None, 1e-9, 10, None, None, None) == smg.EINVAL
     assert L.smg_level_count(None) == 0
+
+
+def test_setup_chain_tables_of_every_transfer(smg):
+    """The chain tables the hierarchy set-up builds (product host code):
+    Table 3's 1216 and 1728 chains for 3d8c / 3d19 / 3d64c and 3d8c / 3d27 /
+    3d64c, the vertex and piecewise-constant pairs, and the x-y
+    semi-coarsening pair (per dimension 2 x 2 = 4 matching (r, q) pairs in x
+    and y for every stencil entry, 1 in z: 16 chains per fine entry), each
+    with a 27-point coarse mask (7 for 3d8c on 7 points)."""
+    off7, off19, off27 = pattern("3d7"), pattern("3d19"), pattern("3d27")
+    assert smg.rap_chain_count(smg.C64C, off19) == (1216, 27)
+    assert smg.rap_chain_count(smg.C64C, off27) == (1728, 27)
+    assert smg.rap_chain_count(smg.C64C, off7) == (8 * 7 * 8, 27)
+    assert smg.rap_chain_count(smg.FW27V, off27) == (2197, 27)
+    assert smg.rap_chain_count(smg.FW27V, off7)[0] == 725
+    assert smg.rap_chain_count(smg.PC8C, off7) == (56, 7)
+    assert smg.rap_chain_count(smg.C16XY, off7) == (16 * 7, 27)
+    assert smg.rap_chain_count(smg.C16XY, off27) == (16 * 27, 27)
+    with pytest.raises(ValueError):
+        smg.rap_chain_count(4, off7)
