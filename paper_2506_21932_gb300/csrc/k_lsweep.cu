@@ -17,11 +17,13 @@
 // of its own first unknown P_c and the next chunk's first unknown P_{c+1},
 // the 128 chunk-first unknowns form a tridiagonal system solved by parallel
 // cyclic reduction through shared memory, and each thread then recovers its
-// rows.  Everything that
-// depends only on the matrix (reciprocal pivots, elimination multipliers,
-// the reduced system's PCR multipliers) is computed once at set-up, so a
-// sweep does no division.  In exact arithmetic the result is the Thomas
-// solution; the rounding differs.
+// rows.  Everything that depends only on the matrix (reciprocal pivots,
+// elimination multipliers, the reduced system's PCR multipliers) is computed
+// once at set-up, so a sweep does no division.  In exact arithmetic the
+// result is the Thomas solution; the rounding differs.  All eight compute
+// warps assemble the right-hand side and store the column; the next
+// column's matrix rows, right-hand side and factors are copied to shared
+// memory (cp.async) while the current column is worked on.
 #include <cstdint>
 #include <utility>
 
@@ -34,9 +36,9 @@ namespace {
 constexpr int kLgsWarps = 8;                       // compute warps of a CTA
 constexpr int kLgsThreads = (kLgsWarps + 2) * 32;  // + publisher + poller
 constexpr int kLgsSolveWarps = 4;                  // warps solving a column (warps 0..3)
-constexpr int kLgsChunks = 32 * kLgsSolveWarps;      // chunks of a column, one per solving thread
-constexpr int kLgsPcr = 7;                           // PCR steps: log2(kLgsChunks)
-constexpr int kLgsMaxM = 8;                          // rows per chunk: nz <= 1024
+constexpr int kLgsChunks = 32 * kLgsSolveWarps;    // chunks of a column, one per solving thread
+constexpr int kLgsPcr = 7;                         // PCR steps: log2(kLgsChunks)
+constexpr int kLgsMaxM = 8;                        // rows per chunk: nz <= 1024
 
 // Column block of the line factors, in doubles, every field kLgsChunks wide:
 // for chunk rows r = 1..m-1 the fields F_W (a_r / den_r), F_INV (1 / den_r),
