@@ -417,7 +417,6 @@ static int setup_level_smoother(smg_ctx* h, Level& L, cudaStream_t st) {
   // plane's CTA for about one L2 round trip, so it is amortised over G steps
   // (at the price of a G-step larger lag between consecutive planes)
   L.cfg.G = 4;
-  if (const char* g = getenv("SMG_SWEEP_G")) L.cfg.G = std::max(1, atoi(g));
   L.cfg.budget_ns = (unsigned long long)h->opt.spin_budget_ms * 1000000ull;
   TRY(dalloc(h, &L.ws, 1));
   SMG_CUDA_TRY(cudaMemsetAsync(L.ws, 0, sizeof(SweepWs), st));
