@@ -522,10 +522,17 @@ __global__ void k_gj_elim(int n, int col, double* M, double* Minv, const double*
   if (f == 0.0) return;
   if (c < n) {
     if (c == col) { M[(long long)r * n + c] = 0.0; return; }
-    M[(long long)r * n + c] -= f * M[(long long)col * n + c];
+    // a zero in the pivot row leaves the entry unchanged: skip its read and
+    // write (the columns already eliminated, and most of the inverse's
+    // columns early on)
+    const double pv = M[(long long)col * n + c];
+    if (pv == 0.0) return;
+    M[(long long)r * n + c] -= f * pv;
   } else {
     c -= n;
-    Minv[(long long)r * n + c] -= f * Minv[(long long)col * n + c];
+    const double pv = Minv[(long long)col * n + c];
+    if (pv == 0.0) return;
+    Minv[(long long)r * n + c] -= f * pv;
   }
 }
 
