@@ -10,7 +10,7 @@
  *   (x slowest, z fastest).  A vector holds B values per point: v[p*B + r].
  * Matrices (Sec. 4.1, SG-DIA): for every point, one coefficient (B == 1) or
  *   one row-major BxB block (B == 3) per stencil offset, offsets in
- *   {-1,0,1}^3 (Sec. 4.2, "Extensibility & Flexibility"):
+ *   {-1,0,1}^3 (Sec. 4.2):
  *   A[((p*nstencil + e)*B + r)*B + c].  Coefficients whose neighbour lies off
  *   the grid must be 0 (zero padding).  The offset list may be given in any
  *   order but must contain the centre, no duplicates and be structurally
@@ -105,13 +105,15 @@ typedef struct {
   int use_graph;
 } smg_options;
 
-/* Build the hierarchy from the finest matrix (Sec. 4.2 "Input Data Format":
- * only the finest A is given).  Levels: halve every dimension while all are
- * even and the smallest is >= 8 (stride-2 full coarsening, Sec. 4.1 P2).
+/* Build the hierarchy from the finest matrix (Sec. 4.2: only the finest A is
+ * given).  Levels: halve every dimension while all are even and the smallest
+ * is >= 8 (stride-2 full coarsening, Sec. 4.1 P2); with the x-y
+ * semi-coarsening transfer only x and y, under the same rule for them.
  * Coarse operators: Galerkin A^C = R A^F P (Eq. 4) evaluated per coarse point
  * by influence chains (Eq. 5-10) derived once on the host from the (R, A, P)
- * patterns.  Smoother set-up per level; dense LU-based inverse of the coarsest
- * level (the paper does not specify the coarsest solve).
+ * patterns.  Smoother set-up per level; dense inverse of the coarsest level
+ * by Gauss-Jordan elimination with partial pivoting (the paper does not
+ * specify the coarsest solve; at most 8192 coarsest unknowns).
  *  out      host: receives the new context (NULL on failure).
  *  dims     host int[3] = {nx, ny, nz}, each >= 1 and <= 4096, ny <= 1024.
  *  nstencil number of offsets, 1..27;  offsets host int[nstencil][3].
@@ -120,8 +122,8 @@ typedef struct {
  *  opt      host, may be NULL (all defaults).
  *  stream   cudaStream_t.
  * Errors: SMG_EINVAL (bad sizes/mask/options, nonzero off-grid coefficient),
- * SMG_ENOMEM, SMG_EBREAKDOWN (zero diagonal, ILU pivot <= 0, singular
- * coarsest matrix), SMG_ECUDA, SMG_ETIMEOUT. */
+ * SMG_ENOMEM, SMG_EBREAKDOWN (zero diagonal, ILU pivot <= 0, a line's Thomas
+ * pivot <= 0, singular coarsest matrix), SMG_ECUDA, SMG_ETIMEOUT. */
 int smg_setup(smg_t* out, const int dims[3], int nstencil, const int* offsets, const double* coeffs, int block,
               const smg_options* opt, void* stream);
 

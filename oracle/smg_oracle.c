@@ -48,7 +48,7 @@ static int find_off(int ns, const int* off, int dx, int dy, int dz) {
   return -1;
 }
 
-/* Mask rules of Sec. 4.2 ("Extensibility & Flexibility"): offsets in {-1,0,1}^3,
+/* Mask rules of Sec. 4.2: offsets in {-1,0,1}^3,
  * no duplicates, the centre present; we additionally require structural symmetry
  * (o in mask <=> -o in mask), which every pattern the paper lists satisfies. */
 int orc_mask_validate(int ns, const int* off) {

@@ -5,7 +5,9 @@
 // anchor of I (R_from, Eq. 6), P as fine offsets from the fine anchor of
 // I+dJ (P_to, Eq. 7), A^F as offsets of v from u (Ngb, Eq. 9) -- a chain
 // (r, a, q) contributes to dJ exactly when
-//     roff[r] + aoff[a] = 2*dJ + poff[q]          (stride-2 coarsening),
+//     roff[r] + aoff[a] = 2*dJ + poff[q]          (stride-2 coarsening;
+//                                                  dJ = aoff in a dimension
+//                                                  that is not coarsened),
 // i.e. when the fine neighbour u+aoff[a] lies in P_to of I+dJ (the
 // intersection of Eq. 10).  The chain set depends only on the three
 // patterns, so it is derived once and reused by every matrix with them.

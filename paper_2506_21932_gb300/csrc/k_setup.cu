@@ -2,8 +2,8 @@
 // (coarse point, coarse stencil entry), summing the influence chains of that
 // entry from a table derived once per pattern triple on the host.  The two
 // products of R A P are fused, as in the paper's generated kernels, so no
-// intermediate A P is stored; "each thread on GPU computing a coarse element"
-// is the mapping the paper names for GPUs (end of Sec. 4.3).
+// intermediate A P is stored; one GPU thread per coarse element is also the
+// mapping the paper suggests for GPUs (end of Sec. 4.3).
 #include "smg_internal.cuh"
 
 namespace {
