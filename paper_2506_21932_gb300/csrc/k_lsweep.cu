@@ -23,7 +23,8 @@
 // result is the Thomas solution; the rounding differs.  All eight compute
 // warps assemble the right-hand side and store the column; the next
 // column's matrix rows, right-hand side and factors are copied to shared
-// memory (cp.async) while the current column is worked on.
+// memory by bulk copies (one thread, mbarrier completion) while the current
+// column is worked on.
 #include <cstdint>
 #include <utility>
 
@@ -175,17 +176,44 @@ struct LsParams {
   int dep;        // previous-plane columns a column reads beyond its own (0 or 1)
 };
 
-// Asynchronous 16-byte global -> shared copies (completion per thread, in
-// commit groups).
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
-               "l"(gsrc)
+// Bulk (TMA, non-tensor) global -> shared copies completing on an mbarrier:
+// one thread issues a column's copies, the transaction count of the barrier
+// tracks their bytes.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the given phase of a copy barrier, bounded by budget_ns; false
+// (and DEV_ERR_TIMEOUT in *err) when the budget runs out.
+__device__ __noinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned long long budget_ns,
+                                               int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > budget_ns) {
+      atomicCAS(err, 0, DEV_ERR_TIMEOUT);
+      return false;
+    }
+  }
 }
 
 // Shared-memory carve-up (doubles): rhs and x of the current column in the
@@ -340,6 +368,7 @@ template <int NS, int KIND, int DIR, bool STAGE>
 __global__ void __launch_bounds__(kLgsThreads, 1) k_lsweep(LsParams P) {
   __shared__ WfShared sh;
   __shared__ int s_abort;
+  __shared__ __align__(8) unsigned long long s_bar[2];  // copy barriers of the two buffers
   extern __shared__ __align__(16) double lgs_sm[];
   const Grid g = P.g;
   const int ns = P.s.ns;
@@ -353,30 +382,38 @@ __global__ void __launch_bounds__(kLgsThreads, 1) k_lsweep(LsParams P) {
   const double* __restrict__ A = P.A;
   const double* __restrict__ b = P.b;
   double* u = P.u;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0]);
+    mbar_init(&s_bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // completed phases of each buffer's barrier (the same count in every thread)
+  unsigned fills[2] = {0u, 0u};
   wf_run(
       sh, P.C,
       [&](int I) {
         const int tid = threadIdx.x, lane = tid & 31;
         const int i = DIR > 0 ? I : g.nx - 1 - I;
-        // copies of column Jn's data into buffer Jn & 1; always one commit group
+        // bulk copies of column Jn's data into buffer Jn & 1, issued by thread 0
+        // (the buffer's previous contents were last read before the barrier
+        // that precedes this call)
         auto prefetch = [&](int Jn) {
-          if (Jn < g.ny) {
+          if (Jn < g.ny && tid == 0) {
             const int jn = DIR > 0 ? Jn : g.ny - 1 - Jn;
             const long long coln = (long long)i * g.ny + jn;
             const int sel = Jn & 1;
-            const double* Fs = P.F + coln * blk;
-            double* Fd = lgs_sm + o_fac + sel * blk;
-            for (int q = 2 * tid; q < blk; q += 2 * kLgsWarps * 32) cp_async16(Fd + q, Fs + q);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const unsigned fb = (unsigned)(blk * sizeof(double));
+            const unsigned ab = STAGE ? (unsigned)(na * sizeof(double)) : 0u;
+            const unsigned bb = STAGE ? (unsigned)(g.nz * sizeof(double)) : 0u;
+            mbar_expect_tx(&s_bar[sel], fb + ab + bb);
+            bulk_copy_g2s(lgs_sm + o_fac + sel * blk, P.F + coln * blk, fb, &s_bar[sel]);
             if (STAGE) {
-              const double* As = A + coln * na;
-              double* Ad = lgs_sm + o_a + sel * na;
-              for (int q = 2 * tid; q < na; q += 2 * kLgsWarps * 32) cp_async16(Ad + q, As + q);
-              const double* bs = b + coln * g.nz;
-              double* bd = lgs_sm + o_b + sel * g.nz;
-              for (int q = 2 * tid; q < g.nz; q += 2 * kLgsWarps * 32) cp_async16(bd + q, bs + q);
+              bulk_copy_g2s(lgs_sm + o_a + sel * na, A + coln * na, ab, &s_bar[sel]);
+              bulk_copy_g2s(lgs_sm + o_b + sel * g.nz, b + coln * g.nz, bb, &s_bar[sel]);
             }
           }
-          cp_async_commit();
         };
         prefetch(0);
         int have_left = kWfDone, have_up = INT_MIN;
@@ -386,11 +423,22 @@ __global__ void __launch_bounds__(kLgsThreads, 1) k_lsweep(LsParams P) {
           prefetch(J + 1);
           if (tid < 32) {
             const int ab = wf_wait(sh, P.C, 0, J, min(J + 1 + P.dep, g.ny), have_left, have_up, lane);
-            if (lane == 0) s_abort = ab;
+            // column J's copies have landed (thread 0 waits; the barrier below
+            // hands the data on to the other threads)
+            if (lane == 0) s_abort = ab || !mbar_wait_bounded(&s_bar[sel], fills[sel] & 1u, P.C.budget_ns, P.C.err);
           }
-          cp_async_wait<1>();  // this thread's copies of column J have landed
+          ++fills[sel];
           lgs_bar();
-          if (s_abort) break;
+          if (s_abort) {
+            // the copies of column J + 1 are in flight: let them land first
+            if (J + 1 < g.ny) {
+              const int s1 = (J + 1) & 1;
+              if (tid == 0) mbar_wait_bounded(&s_bar[s1], fills[s1] & 1u, P.C.budget_ns, P.C.err);
+              ++fills[s1];
+              lgs_bar();
+            }
+            break;
+          }
           unsigned xymask = 0;
 #pragma unroll
           for (int a = -1; a <= 1; ++a)
@@ -450,8 +498,6 @@ __global__ void __launch_bounds__(kLgsThreads, 1) k_lsweep(LsParams P) {
           lgs_bar();  // the column's stores precede the release below
           if (tid == 0) wf_st_rel_cta(&sh.wdone[0], J + 1);
         }
-        cp_async_wait<0>();  // no copy may land after the CTA moves on
-        lgs_bar();
         if (tid == 0) wf_st_rel_cta(&sh.wdone[0], kWfDone);
       },
       kLgsWarps);
