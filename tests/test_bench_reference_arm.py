@@ -1,0 +1,35 @@
+"""The benchmark's reference arm (the CPU oracle on a bounded sample of a
+workload) runs without a GPU and prints one JSON line with the contract's
+keys; the GPU arm's configuration labels cover every workload."""
+import json
+import os
+import subprocess
+import sys
+
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_the_contract_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "c1",
+                        "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["higher_is_better"] is False and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["config"]["workload"].startswith("poisson7_32^3")
+
+
+def test_every_workload_has_a_label():
+    sys.path.insert(0, ROOT)
+    import bench
+    for name, w in bench.WORKLOADS.items():
+        assert w["smoother"] in (0, 1, 2) and w["transfer"] in (0, 1, 2, 3) and w["krylov"] in (0, 1, 2), name
+        assert w["gen"] in ("lap", "q1", "q1z", "fv", "blk"), name
+        assert len(w["dims"]) == 3 and w["tol"] > 0, name
