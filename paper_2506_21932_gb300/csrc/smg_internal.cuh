@@ -203,9 +203,10 @@ cudaError_t launch_ilu_factor(Grid g, const Stencil& s, const double* A, double*
                               const int* upd, int nupd, SweepWs* ws, int* err, const SweepCfg& cfg, cudaStream_t st);
 
 // Line Gauss-Seidel along z (FP64, one unknown per point).  A column of nz
-// points is solved by one warp in 32 chunks of lgs_chunk_rows(nz) rows; its
-// matrix-only factors take lgs_block_doubles(nz) doubles per column, columns
-// in (i, j) order.  lgs_supported: the mask holds the centre and nz <= 1024.
+// points is solved by four warps in 128 chunks of lgs_chunk_rows(nz) rows;
+// its matrix-only factors take lgs_block_doubles(nz) doubles per column,
+// columns in (i, j) order.  lgs_supported: the mask holds the centre and
+// nz <= 1024.
 int lgs_chunk_rows(int nz);
 long long lgs_block_doubles(int nz);
 bool lgs_supported(const Grid& g, const Stencil& s);
