@@ -1,7 +1,7 @@
 """Parity of the GPU line Gauss-Seidel smoother (LGS along z) with the
 oracle's Thomas-algorithm line sweeps, through the C ABI.
 
-The GPU solves each column by a partitioned elimination (32 chunks, parallel
+The GPU solves each column by a partitioned elimination (128 chunks, parallel
 cyclic reduction on the chunk interface) instead of the serial Thomas
 recurrence: the same solution in exact arithmetic, with a different rounding
 order.  The column systems here are diagonally dominant (condition numbers
