@@ -1,7 +1,9 @@
 /*
  * smg_oracle.c -- plain, slow, single-threaded FP64 reference of the StructMG
- * hot path (arXiv 2506.21932): stencil Galerkin coarsening, dependence-preserving
- * Gauss-Seidel and ILU(0) smoothers, V-cycle, PCG / flexible PCG / FGMRES.
+ * hot path (arXiv 2506.21932): stencil Galerkin coarsening with the vertex,
+ * cell-centred and x-y semi-coarsening transfer pairs, dependence-preserving
+ * Gauss-Seidel, ILU(0) and line (z) Gauss-Seidel smoothers, V-cycle, PCG /
+ * flexible PCG / FGMRES.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this code:
  * only the tests, the package's smoke check and the benchmark's CPU-baseline leg
