@@ -132,6 +132,20 @@ int smg_setup(smg_t* out, const int dims[3], int nstencil, const int* offsets, c
  * Errors: SMG_EINVAL (NULL handle/pointers), SMG_ECUDA, SMG_ETIMEOUT. */
 int smg_vcycle(smg_t h, const double* r, double* z, void* stream);
 
+/* Profiled V-cycle: the same z = M^{-1} r as smg_vcycle (always run eagerly,
+ * never from a captured graph), with a CUDA event recorded on the stream
+ * after every stage, so the device time of each stage is measured without
+ * host gaps.  Stage t (0 <= t < *count) ran on level levels[t]; stages[t] is
+ * one of SMG_STAGE_*; ms[t] its device time.  At most cap entries are
+ * written (*count is the full number).  Synchronises the stream.  Not part
+ * of the method: a measurement aid for the per-level cost of a cycle.
+ * Errors: SMG_EINVAL (NULL or aliased pointers, cap < 0), SMG_ECUDA. */
+enum { SMG_STAGE_PRE1 = 1, SMG_STAGE_PRE2 = 2, SMG_STAGE_RESIDUAL = 3, SMG_STAGE_RESTRICT = 4,
+       SMG_STAGE_COARSE = 5, SMG_STAGE_PROLONG = 6, SMG_STAGE_POST_RESIDUAL = 7, SMG_STAGE_POST1 = 8,
+       SMG_STAGE_POST2 = 9, SMG_STAGE_POST_ADD = 10, SMG_STAGE_CAST = 11, SMG_STAGE_LEARNED = 12 };
+int smg_vcycle_profile(smg_t h, const double* r, double* z, int cap, int* count, int* levels, int* stages,
+                       float* ms, void* stream);
+
 /* Solve A x = b with the Krylov method of the options, preconditioned by one
  * V-cycle per iteration (Sec. 5.2), until ||r_k||_2 / ||b||_2 < tol (Table 8).
  *  b      device double [n*B];  x  device double [n*B]: initial guess in,
@@ -224,6 +238,17 @@ long long smg_launch_count(void);
  * Returns SMG_ETIMEOUT when the wait ran out as designed (the context stays
  * usable), SMG_EINVAL for bad arguments, SMG_ECUDA on a CUDA failure. */
 int smg_selftest_wait(smg_t h, int budget_ms, void* stream);
+
+/* Replaces the bound of every device-side wait of the context's kernels
+ * (smg_options.spin_budget_ms at set-up) by budget_ns nanoseconds, 0 <=
+ * budget_ns <= 10 s.  With 0, a wait that is not satisfied at its first check
+ * gives up at once: the kernels then take their abort path (error word set,
+ * every CTA drains, bulk copies in flight are waited for with a fixed bound
+ * of their own) and the call that launched them returns SMG_ETIMEOUT, after
+ * which the context is unchanged and usable -- the failure path can be
+ * exercised without a GPU fault.  A captured V-cycle graph is dropped (it
+ * holds the old bound).  Host-only; SMG_EINVAL for a bad handle or budget. */
+int smg_set_wait_budget_ns(smg_t h, long long budget_ns);
 
 /* ---------------------------------------------------------------------------
  * Host-only symbolic derivation of influence chains (Sec. 4.3, Eq. 5-10).

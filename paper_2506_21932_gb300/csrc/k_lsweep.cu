@@ -203,6 +203,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 }
 // Waits for the given phase of a copy barrier, bounded by budget_ns; false
 // (and DEV_ERR_TIMEOUT in *err) when the budget runs out.
+// Bound of the waits that drain a plane's bulk copies after an abort.
+constexpr unsigned long long kLgsDrainNs = 100ull * 1000 * 1000;
+
 __device__ __noinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned long long budget_ns,
                                                int* err) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -369,6 +372,7 @@ __global__ void __launch_bounds__(kLgsThreads, 1) k_lsweep(LsParams P) {
   __shared__ WfShared sh;
   __shared__ int s_abort;
   __shared__ __align__(8) unsigned long long s_bar[2];  // copy barriers of the two buffers
+  __shared__ int s_landed, s_broken;
   extern __shared__ __align__(16) double lgs_sm[];
   const Grid g = P.g;
   const int ns = P.s.ns;
@@ -385,6 +389,7 @@ __global__ void __launch_bounds__(kLgsThreads, 1) k_lsweep(LsParams P) {
   if (threadIdx.x == 0) {
     mbar_init(&s_bar[0]);
     mbar_init(&s_bar[1]);
+    s_broken = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(kLgsThreads, 1) k_lsweep(LsParams P) {
         // (the buffer's previous contents were last read before the barrier
         // that precedes this call)
         auto prefetch = [&](int Jn) {
-          if (Jn < g.ny && tid == 0) {
+          if (Jn < g.ny && tid == 0 && !s_broken) {
             const int jn = DIR > 0 ? Jn : g.ny - 1 - Jn;
             const long long coln = (long long)i * g.ny + jn;
             const int sel = Jn & 1;
@@ -415,6 +420,15 @@ __global__ void __launch_bounds__(kLgsThreads, 1) k_lsweep(LsParams P) {
             }
           }
         };
+        if (s_broken) {
+          // a drain gave up earlier: the copy barriers' phases are unknown, so
+          // this CTA issues no more copies and releases its planes at once
+          if (tid == 0) {
+            wf_st_rel_cta(&sh.abort_flag, 1);
+            wf_st_rel_cta(&sh.wdone[0], kWfDone);
+          }
+          return;
+        }
         prefetch(0);
         int have_left = kWfDone, have_up = INT_MIN;
         for (int J = 0; J < g.ny; ++J) {
@@ -423,22 +437,34 @@ __global__ void __launch_bounds__(kLgsThreads, 1) k_lsweep(LsParams P) {
           prefetch(J + 1);
           if (tid < 32) {
             const int ab = wf_wait(sh, P.C, 0, J, min(J + 1 + P.dep, g.ny), have_left, have_up, lane);
-            // column J's copies have landed (thread 0 waits; the barrier below
-            // hands the data on to the other threads)
-            if (lane == 0) s_abort = ab || !mbar_wait_bounded(&s_bar[sel], fills[sel] & 1u, P.C.budget_ns, P.C.err);
+            // column J's copies have landed (thread 0 waits, whether or not
+            // the dependency wait gave up; the barrier below hands the data on
+            // to the other threads)
+            if (lane == 0) {
+              const bool landed = mbar_wait_bounded(&s_bar[sel], fills[sel] & 1u, P.C.budget_ns, P.C.err);
+              s_landed = landed;
+              s_abort = ab || !landed;
+            }
           }
-          ++fills[sel];
           lgs_bar();
           if (s_abort) {
-            // the copies of column J + 1 are in flight: let them land first
-            if (J + 1 < g.ny) {
-              const int s1 = (J + 1) & 1;
-              if (tid == 0) mbar_wait_bounded(&s_bar[s1], fills[s1] & 1u, P.C.budget_ns, P.C.err);
-              ++fills[s1];
-              lgs_bar();
+            // drain every copy issued before leaving the plane: column J's if
+            // its wait gave up, column J + 1's always.  The drain bound does
+            // not depend on the wait budget (a copy lands in microseconds).
+            if (tid == 0) {
+              bool ok = s_landed || mbar_wait_bounded(&s_bar[sel], fills[sel] & 1u, kLgsDrainNs, P.C.err);
+              if (J + 1 < g.ny) {
+                const int s1 = (J + 1) & 1;
+                ok = mbar_wait_bounded(&s_bar[s1], fills[s1] & 1u, kLgsDrainNs, P.C.err) && ok;
+              }
+              if (!ok) s_broken = 1;
             }
+            ++fills[sel];
+            if (J + 1 < g.ny) ++fills[(J + 1) & 1];
+            lgs_bar();
             break;
           }
+          ++fills[sel];
           unsigned xymask = 0;
 #pragma unroll
           for (int a = -1; a <= 1; ++a)

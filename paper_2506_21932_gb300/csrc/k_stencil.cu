@@ -2,6 +2,7 @@
 // transfers (Sec. 2 V-cycle; Table 3 patterns 3d27v, 3d8c and 3d64c, and the
 // 2d4c / 2d16c pair of x-y semi-coarsening), precision
 // casts and lowering, diagonal inverses and the dense coarsest level.
+#include "ilurec.cuh"
 #include "smg_internal.cuh"
 
 namespace {
@@ -394,6 +395,37 @@ __global__ void k_lower(Grid g, Stencil s, const double* __restrict__ A, int pk,
   for (int e = 0; e < s.ns; ++e) v[e] = __double2bfloat16(a[e] / (double)(e < s.ec ? sl : su));
 }
 
+// Split ILU(0) records (ilurec.cuh) of every point, from the FP64 factors.
+// The values and scales equal those of k_lower(split = 1) entry by entry.
+template <int PK, int NS>
+__global__ void k_ilu_split(Grid g, const double* __restrict__ LU, const double* __restrict__ udinv, void* Lrec,
+                            void* Urec) {
+  using Val = typename Prec<PK>::val;
+  using RL = IluRec<PK, NS, false>;
+  using RU = IluRec<PK, NS, true>;
+  constexpr int EC = Shape<NS>::EC;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.n) return;
+  const double* a = LU + p * NS;
+  unsigned char* lr = (unsigned char*)Lrec + p * RL::BYTES;
+  unsigned char* ur = (unsigned char*)Urec + p * RU::BYTES;
+  for (int t = 0; t < RL::CHUNKS; ++t) ((uint4*)lr)[t] = make_uint4(0, 0, 0, 0);
+  for (int t = 0; t < RU::CHUNKS; ++t) ((uint4*)ur)[t] = make_uint4(0, 0, 0, 0);
+  Val* lv = (Val*)lr;
+  Val* uv = (Val*)ur;
+  if constexpr (PK == KBF) {
+    const float sl = row_scale(a, 0, EC), su = row_scale(a, EC + 1, NS);
+    for (int e = 0; e < EC; ++e) lv[e] = __double2bfloat16(a[e] / (double)sl);
+    for (int e = EC + 1; e < NS; ++e) uv[e - EC - 1] = __double2bfloat16(a[e] / (double)su);
+    *(float*)(lr + RL::S_OFF) = sl;
+    *(float*)(ur + RU::S_OFF) = su;
+  } else {
+    for (int e = 0; e < EC; ++e) lv[e] = (Val)a[e];
+    for (int e = EC + 1; e < NS; ++e) uv[e - EC - 1] = (Val)a[e];
+    *(Val*)(ur + RU::D_OFF) = (Val)udinv[p];
+  }
+}
+
 // Stencil entries reordered: out[p][e] = in[p][perm[e]] (BxB blocks).
 __global__ void k_permute(long long n, int ns, int bb, const int* __restrict__ perm, const double* __restrict__ in,
                           double* __restrict__ out) {
@@ -665,6 +697,25 @@ cudaError_t launch_check_padding(Grid g, const Stencil& s, int B, const double* 
 cudaError_t launch_lower_matrix(Grid g, const Stencil& s, const double* A, int pk, int split, void* vals, float* scale,
                                 float* scale2, cudaStream_t st) {
   k_lower<<<div_up(g.n, TPB), TPB, 0, st>>>(g, s, A, pk, split, vals, scale, scale2);
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ilu_split(Grid g, int ns, int pk, const double* LU, const double* udinv, void* Lrec, void* Urec,
+                             cudaStream_t st) {
+  const int nb = div_up(g.n, TPB);
+#define SPLIT_(PK, NS) k_ilu_split<PK, NS><<<nb, TPB, 0, st>>>(g, LU, udinv, Lrec, Urec)
+  if (pk == K64) {
+    if (ns == 27) SPLIT_(K64, 27); else if (ns == 19) SPLIT_(K64, 19); else if (ns == 7) SPLIT_(K64, 7);
+    else return cudaErrorInvalidValue;
+  } else if (pk == K32) {
+    if (ns == 27) SPLIT_(K32, 27); else if (ns == 19) SPLIT_(K32, 19); else if (ns == 7) SPLIT_(K32, 7);
+    else return cudaErrorInvalidValue;
+  } else {
+    if (ns == 27) SPLIT_(KBF, 27); else if (ns == 19) SPLIT_(KBF, 19); else if (ns == 7) SPLIT_(KBF, 7);
+    else return cudaErrorInvalidValue;
+  }
+#undef SPLIT_
   smg_count_launch(1);
   return cudaGetLastError();
 }

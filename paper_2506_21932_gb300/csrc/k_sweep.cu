@@ -277,7 +277,7 @@ cudaError_t launch_sweep(const LevelView& L, int kind, int dir, const void* M, c
                          const void* dinv, double w, const void* b, void* u, SweepWs* ws, int* err,
                          const SweepCfg& cfg, cudaStream_t st) {
   {
-    cudaError_t e3 = launch_sweep3(L, kind, dir, M, sc1, sc2, dinv, w, b, u, ws, err, cfg, st);
+    cudaError_t e3 = launch_sweep3(L, kind, dir, M, sc1, sc2, dinv, w, b, u, ws, err, cfg, st, false);
     if (e3 != cudaErrorNotSupported) return e3;
     cudaError_t e2 = launch_sweep2(L, kind, dir, M, sc1, sc2, dinv, w, b, u, ws, err, cfg, st);
     if (e2 != cudaErrorNotSupported) return e2;

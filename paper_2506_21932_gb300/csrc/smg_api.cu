@@ -10,6 +10,7 @@
 
 #include "chains.h"
 #include "cnn.cuh"
+#include "ilurec.cuh"
 #include "krylov.cuh"
 #include "smg_internal.cuh"
 
@@ -73,6 +74,8 @@ struct Level {
   SweepCfg cfg{};
   int* ilu_upd = nullptr;
   double* lf = nullptr;     // line Gauss-Seidel: per-column factors
+  void* Lrec = nullptr;     // ILU(0): split L / U records of the working precision (ilurec.cuh)
+  void* Urec = nullptr;
 };
 
 struct smg_ctx {
@@ -102,7 +105,31 @@ struct smg_ctx {
   CnnWork ls_w{};
   double *ls_r = nullptr, *ls_d = nullptr, *ls_t = nullptr;
   double* ls_dinv = nullptr;  // 1 / a_pp of the finest matrix: scales the network output
+  // V-cycle profiling (smg_vcycle_profile): an event after every launch
+  bool prof_on = false;
+  int prof_n = 0;
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_level, prof_code;
 };
+
+// Records a profiling event after the launches of one stage (no-op unless a
+// profiled V-cycle is running).
+enum { PM_START = 0, PM_PRE1, PM_PRE2, PM_RESID, PM_RESTRICT, PM_COARSE, PM_PROLONG, PM_POST_RESID, PM_POST1,
+       PM_POST2, PM_POST_ADD, PM_CAST, PM_LEARNED };
+static void prof_mark(smg_ctx* h, int level, int code, cudaStream_t st) {
+  if (!h->prof_on) return;
+  if (h->prof_n >= (int)h->prof_ev.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    h->prof_ev.push_back(e);
+    h->prof_level.push_back(0);
+    h->prof_code.push_back(0);
+  }
+  cudaEventRecord(h->prof_ev[h->prof_n], st);
+  h->prof_level[h->prof_n] = level;
+  h->prof_code[h->prof_n] = code;
+  ++h->prof_n;
+}
 
 static int dev_alloc(smg_ctx* h, void** p, size_t bytes) {
   *p = nullptr;
@@ -130,6 +157,7 @@ static void free_ctx(smg_ctx* h) {
   }
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
+  for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   if (h->hsc) cudaFreeHost(h->hsc);
   if (h->herr) cudaFreeHost(h->herr);
@@ -196,6 +224,12 @@ static int sweep(smg_ctx* h, Level& L, int kind, int dir, const void* b, void* u
   const void* M;
   const float *s1 = nullptr, *s2 = nullptr;
   const void* dv;
+  if ((kind == SW_ILU_L || kind == SW_ILU_U) && L.Lrec) {
+    SMG_CUDA_TRY(launch_sweep3(v, kind, dir, kind == SW_ILU_L ? L.Lrec : L.Urec, nullptr, nullptr,
+                               lp ? L.dinv32 : (const void*)L.udinv, h->opt.relax_w, b, u, L.ws, h->err, L.cfg, st,
+                               true));
+    return SMG_OK;
+  }
   if (kind == SW_ILU_L || kind == SW_ILU_U) {
     M = lp ? L.LUv : (const void*)L.LU;
     s1 = L.Ls;
@@ -217,32 +251,44 @@ static int lsweep(smg_ctx* h, Level& L, int kind, int dir, const void* b, void* 
   return SMG_OK;
 }
 
-static int smooth_pre(smg_ctx* h, Level& L, const void* f, void* u, cudaStream_t st) {
+static int smooth_pre(smg_ctx* h, Level& L, int l, const void* f, void* u, cudaStream_t st) {
   if (h->opt.smoother == SMG_SMOOTHER_LGS) {
     TRY(lsweep(h, L, SW_GS_ZERO, +1, f, u, st));
+    prof_mark(h, l, PM_PRE1, st);
     TRY(lsweep(h, L, SW_GS_FULL, -1, f, u, st));
   } else if (h->opt.smoother == SMG_SMOOTHER_SGS) {
     TRY(sweep(h, L, SW_GS_ZERO, +1, f, u, st));
+    prof_mark(h, l, PM_PRE1, st);
     TRY(sweep(h, L, SW_GS_FULL, -1, f, u, st));
   } else {
     TRY(sweep(h, L, SW_ILU_L, +1, f, u, st));
+    prof_mark(h, l, PM_PRE1, st);
     TRY(sweep(h, L, SW_ILU_U, -1, u, u, st));
   }
+  prof_mark(h, l, PM_PRE2, st);
   return SMG_OK;
 }
 
-static int smooth_post(smg_ctx* h, Level& L, const void* f, void* u, cudaStream_t st) {
+static int smooth_post(smg_ctx* h, Level& L, int l, const void* f, void* u, cudaStream_t st) {
   if (h->opt.smoother == SMG_SMOOTHER_LGS) {
     TRY(lsweep(h, L, SW_GS_FULL, +1, f, u, st));
+    prof_mark(h, l, PM_POST1, st);
     TRY(lsweep(h, L, SW_GS_FULL, -1, f, u, st));
+    prof_mark(h, l, PM_POST2, st);
   } else if (h->opt.smoother == SMG_SMOOTHER_SGS) {
     TRY(sweep(h, L, SW_GS_FULL, +1, f, u, st));
+    prof_mark(h, l, PM_POST1, st);
     TRY(sweep(h, L, SW_GS_FULL, -1, f, u, st));
+    prof_mark(h, l, PM_POST2, st);
   } else {
     SMG_CUDA_TRY(launch_spmv(view(h, L, true), u, f, L.t, 1, st));
+    prof_mark(h, l, PM_POST_RESID, st);
     TRY(sweep(h, L, SW_ILU_L, +1, L.t, L.t, st));
+    prof_mark(h, l, PM_POST1, st);
     TRY(sweep(h, L, SW_ILU_U, -1, L.t, L.t, st));
+    prof_mark(h, l, PM_POST2, st);
     SMG_CUDA_TRY(vec_add(L.g.n * L.B, L.t, u, h->pk == K64, h->rw, st));
+    prof_mark(h, l, PM_POST_ADD, st);
   }
   return SMG_OK;
 }
@@ -289,11 +335,13 @@ static int vcycle_body(smg_ctx* h, const double* r, double* z, cudaStream_t st) 
   const long long n0 = L0.g.n * h->B;
   const void* f0;
   void* u0;
+  prof_mark(h, 0, PM_START, st);
   if (h->pk == K64) {
     f0 = r;
     u0 = z;
   } else {
     SMG_CUDA_TRY(launch_cast_d2f(r, (float*)L0.f, n0, st));
+    prof_mark(h, 0, PM_CAST, st);
     f0 = L0.f;
     u0 = L0.u;
   }
@@ -301,18 +349,28 @@ static int vcycle_body(smg_ctx* h, const double* r, double* z, cudaStream_t st) 
   auto U = [&](int l) -> void* { return l == 0 ? u0 : h->L[l].u; };
   for (int l = 0; l < nl - 1; ++l) {
     Level& L = h->L[l];
-    TRY(smooth_pre(h, L, F(l), U(l), st));
+    TRY(smooth_pre(h, L, l, F(l), U(l), st));
     SMG_CUDA_TRY(launch_spmv(view(h, L, true), U(l), F(l), L.t, 1, st));
+    prof_mark(h, l, PM_RESID, st);
     SMG_CUDA_TRY(launch_restrict(h->opt.transfer, L.g, h->B, h->pk, L.t, h->L[l + 1].f, st));
+    prof_mark(h, l, PM_RESTRICT, st);
   }
   TRY(coarse_solve(h, F(nl - 1), U(nl - 1), st));
+  prof_mark(h, nl - 1, PM_COARSE, st);
   for (int l = nl - 2; l >= 0; --l) {
     Level& L = h->L[l];
     SMG_CUDA_TRY(launch_prolong_add(h->opt.transfer, L.g, h->B, h->pk, h->L[l + 1].u, U(l), st));
-    TRY(smooth_post(h, L, F(l), U(l), st));
+    prof_mark(h, l, PM_PROLONG, st);
+    TRY(smooth_post(h, L, l, F(l), U(l), st));
   }
-  if (h->pk != K64) SMG_CUDA_TRY(launch_cast_f2d((const float*)u0, z, n0, st));
-  if (h->ls_logk) TRY(learned_post_smooth(h, r, z, st));
+  if (h->pk != K64) {
+    SMG_CUDA_TRY(launch_cast_f2d((const float*)u0, z, n0, st));
+    prof_mark(h, 0, PM_CAST, st);
+  }
+  if (h->ls_logk) {
+    TRY(learned_post_smooth(h, r, z, st));
+    prof_mark(h, 0, PM_LEARNED, st);
+  }
   return SMG_OK;
 }
 
@@ -462,6 +520,12 @@ static int setup_level_smoother(smg_ctx* h, Level& L, cudaStream_t st) {
       SMG_CUDA_TRY(launch_lower_matrix(L.g, L.s, L.LU, h->pk, 1, L.LUv, L.Ls, L.Us, st));
       SMG_CUDA_TRY(launch_d2f_array(L.udinv, (float*)L.dinv32, n, st));
     }
+  }
+  // ILU(0) triangular solves on the warp-pipelined kernel read split records
+  if (h->opt.smoother == SMG_SMOOTHER_ILU0 && sweep3_supported(view(h, L, true), SW_ILU_L)) {
+    TRY(dev_alloc(h, &L.Lrec, (size_t)n * ilu_rec_bytes(h->pk, L.s.ns, false)));
+    TRY(dev_alloc(h, &L.Urec, (size_t)n * ilu_rec_bytes(h->pk, L.s.ns, true)));
+    SMG_CUDA_TRY(launch_ilu_split(L.g, L.s.ns, h->pk, L.LU, L.udinv, L.Lrec, L.Urec, st));
   }
   return SMG_OK;
 }
@@ -705,6 +769,26 @@ extern "C" int smg_stats(smg_t h, smg_stats_t* out) {
   if (!h || !out) return SMG_EINVAL;
   *out = h->stats;
   return SMG_OK;
+}
+
+extern "C" int smg_vcycle_profile(smg_t h, const double* r, double* z, int cap, int* count, int* levels,
+                                  int* stages, float* ms, void* stream) {
+  if (!h || !r || !z || r == z || !count || cap < 0 || (cap > 0 && (!levels || !stages || !ms))) return SMG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->prof_on = true;
+  h->prof_n = 0;
+  const int rc = vcycle_body(h, r, z, st);
+  h->prof_on = false;
+  TRY(rc);
+  SMG_CUDA_TRY(cudaStreamSynchronize(st));
+  const int n = h->prof_n - 1;
+  *count = n;
+  for (int t = 0; t < n && t < cap; ++t) {
+    levels[t] = h->prof_level[t + 1];
+    stages[t] = h->prof_code[t + 1];
+    SMG_CUDA_TRY(cudaEventElapsedTime(&ms[t], h->prof_ev[t], h->prof_ev[t + 1]));
+  }
+  return fetch_err(h, st);
 }
 
 extern "C" int smg_vcycle(smg_t h, const double* r, double* z, void* stream) {
@@ -1077,6 +1161,16 @@ extern "C" int smg_set_learned_smoother(smg_t h, const float* theta, const doubl
     h->vgraph = nullptr;
   }
   SMG_CUDA_TRY(cudaStreamSynchronize(st));
+  return SMG_OK;
+}
+
+extern "C" int smg_set_wait_budget_ns(smg_t h, long long budget_ns) {
+  if (!h || budget_ns < 0 || budget_ns > 10000000000LL) return SMG_EINVAL;
+  for (int l = 0; l < h->nlev; ++l) h->L[l].cfg.budget_ns = (unsigned long long)budget_ns;
+  if (h->vgraph) {
+    cudaGraphExecDestroy(h->vgraph);
+    h->vgraph = nullptr;
+  }
   return SMG_OK;
 }
 

@@ -178,10 +178,13 @@ cudaError_t launch_sweep2(const LevelView& L, int kind, int dir, const void* M, 
 
 // Warp-pipelined variant (same masks, ny <= 512): per-warp time loops synced
 // through shared-memory counters, a communication warp for the GPU-scope
-// hand-off; returns cudaErrorNotSupported when it does not apply.
+// hand-off; returns cudaErrorNotSupported when it does not apply.  rec: the
+// ILU operand M is the split L / U records of ilurec.cuh (FP32 / BF16 ILU
+// solves exist only in that form) instead of the factors [n][ns].
+bool sweep3_supported(const LevelView& L, int kind);
 cudaError_t launch_sweep3(const LevelView& L, int kind, int dir, const void* M, const float* sc1, const float* sc2,
                           const void* dinv, double w, const void* b, void* u, SweepWs* ws, int* err,
-                          const SweepCfg& cfg, cudaStream_t st);
+                          const SweepCfg& cfg, cudaStream_t st, bool rec);
 
 // Bounded wait on a flag nobody sets (failure-path self-test).
 cudaError_t launch_wait_selftest(const int* flag, int* err, unsigned long long budget_ns, cudaStream_t st);

@@ -1,0 +1,563 @@
+// Kernel template of the warp-pipelined wavefront sweeps, included by one
+// translation unit per working precision (k_sweep3*.cu).
+#pragma once
+// Warp-pipelined wavefront sweeps (exact lexicographic order) for the
+// 7/19/27-point masks with one unknown per point: Gauss-Seidel (zero-guess
+// and full, both directions) and the two ILU(0) triangular solves (Sec. 4.4).
+//
+// Schedule: point (i,j,k) runs at global time t = SA*i + SB*j + k (the
+// smallest skews that put every lower neighbour strictly earlier).
+//  * A CTA owns W consecutive x-planes (handed out by an atomic ticket, so a
+//    CTA only ever waits on planes that running CTAs own).  Each plane is cut
+//    into warps of 32 y-columns, one lane per column, and every warp runs its
+//    own loop over local steps s = t - SA*plane; lane J treats point
+//    K = s - SB*J of its column at step s.
+//  * A neighbour of the lower triangle is older than its point by a fixed
+//    number of steps, its slack (SA*dx' + SB*dy' + dz' in sweep coordinates).
+//    Previous-plane values are loaded as late as their slack allows: with a
+//    lookahead of X steps, a term of slack sigma is loaded min(2, sigma+X-1)
+//    steps before its point is finished, so a warp of the next plane only
+//    needs the previous plane to be SA + X steps ahead (X = 0 for FP64,
+//    whose long instruction latency hides the one load issued in the step;
+//    X = 1 for FP32 / BF16).
+//  * Inside a step: wait for the three counters it depends on (left warp,
+//    right warp for the shared value ring, previous plane), issue the loads
+//    whose slack is one step, pre-sum point K+1 (every term that is already
+//    final), finish point K (own column, left column, the late
+//    previous-plane terms), store it, publish the step, then load the
+//    operands of K+1 and K+2.  The pre-sum of K+1 runs while the in-step
+//    loads are in flight.
+//  * Counters are per warp in shared memory (CTA-scope acquire/release); one
+//    publisher warp copies the last plane's counters to global memory
+//    (GPU-scope release) and one poller warp copies the previous CTA's into
+//    shared memory (GPU-scope acquire), so compute warps never execute a
+//    GPU-scope fence.  One CTA per SM (the launch reserves more than half of
+//    the shared memory) and the grid is capped at the SM count.
+//  * The ILU solves read split, 16-byte-aligned records (ilurec.cuh): a lower
+//    solve streams only L, an upper solve only U and 1/u_pp.
+// Every wait is bounded; on expiry the error word is set and all CTAs drain.
+#include <algorithm>
+#include <climits>
+
+#include "ilurec.cuh"
+#include "shapes.cuh"
+#include "smg_internal.cuh"
+
+namespace sweep3 {
+
+// Term classes, relative to the sweep direction.
+enum { T_SKIP = 0, T_OWN = 1, T_Y = 2, T_X = 3, T_OLD = 4 };
+
+template <int NS, int KIND, int DIR>
+__host__ __device__ constexpr int cls(int e) {
+  using S = Shape<NS>;
+  const int sx = DIR * S::o(e, 0), sy = DIR * S::o(e, 1), sz = DIR * S::o(e, 2);
+  if (e == S::EC) return T_SKIP;
+  const bool is_new = sx < 0 || (sx == 0 && (sy < 0 || (sy == 0 && sz < 0)));
+  if (!is_new) return KIND == SW_GS_FULL ? T_OLD : T_SKIP;
+  if (sx == 0 && sy == 0) return T_OWN;  // (0, 0, -1)
+  if (sx == 0) return T_Y;               // (0, -1, *): the left column
+  return T_X;                            // (-1, *, *): the previous plane
+}
+
+// Steps between a new neighbour and its point.
+template <int NS, int DIR>
+__host__ __device__ constexpr int slack(int e) {
+  using S = Shape<NS>;
+  return -(S::SA * DIR * S::o(e, 0) + S::SB * DIR * S::o(e, 1) + DIR * S::o(e, 2));
+}
+
+// When an operand is consumed: in the pre-sum of K+1 (loaded two steps
+// ahead), or in the finish of K (loaded one step ahead, or in the step).
+enum { U_NONE = 0, U_PRE = 1, U_FIN1 = 2, U_FIN0 = 3, U_FINR = 4 };
+
+template <int NS, int KIND, int DIR, int X>
+__host__ __device__ constexpr int use(int e) {
+  const int c = cls<NS, KIND, DIR>(e);
+  if (c == T_SKIP) return U_NONE;
+  if (c == T_OLD) return U_PRE;
+  if (c == T_OWN) return U_FINR;
+  const int sg = slack<NS, DIR>(e);
+  if (c == T_Y) return sg >= 2 ? U_PRE : U_FINR;  // left column, from the shared ring
+  const int m = sg + X - 1 < 2 ? sg + X - 1 : 2;  // previous plane
+  return m == 2 ? U_PRE : (m == 1 ? U_FIN1 : U_FIN0);
+}
+
+struct Sweep3Params {
+  Grid g;
+  unsigned long long budget_ns;
+  const void* M;       // GS: matrix [n][NS]; ILU: split records (REC) or the factors [n][NS]
+  const float* scale;  // KBF row scale of M (GS and unsplit ILU)
+  const void* dinv;    // GS: inverse diagonal; ILU_U: 1/u_pp where the record has none
+  double w;
+  const void* b;  // may alias u
+  void* u;
+  SweepWs* ws;    // prog[] indexed by plane group
+  int* err;
+  int lin[27];
+};
+
+constexpr int kMaxWarpsPerPlane = 16;  // ny <= 512
+constexpr int kMaxThreads = 576;       // 16 compute + 2 communication warps
+constexpr int kPrefetch = 10;
+constexpr int kDone = INT_MAX / 2;
+constexpr size_t kOneCtaPerSmSmem = 120 * 1024;
+constexpr unsigned kPublishGapNs = 100;
+// Shared ring of the last kRing values of every column.  A column's value
+// at point k is overwritten by point k + kRing.  A warp publishes step s
+// once point k is stored, before it reads the ring for point k+1, so its
+// left-hand neighbour may run at most kRing - SB - 2 steps ahead of the
+// published step without overwriting a value still to be read.
+constexpr int kRing = 16;
+
+__device__ __forceinline__ int ld_acq_cta(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel_cta(int* p, int v) {
+  asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// 32-bit word wi of a record held in registers (wi a compile-time constant
+// after unrolling, so this is a register selection), and value `slot`.
+template <int CH>
+__device__ __forceinline__ unsigned rec_word(const uint4 (&q)[CH], int wi) {
+  const uint4 v = q[wi >> 2];
+  const int c = wi & 3;
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+template <typename Val, int CH>
+__device__ __forceinline__ Val rec_val(const uint4 (&q)[CH], int slot) {
+  if constexpr (sizeof(Val) == 8) {
+    return __hiloint2double((int)rec_word(q, 2 * slot + 1), (int)rec_word(q, 2 * slot));
+  } else if constexpr (sizeof(Val) == 4) {
+    return __uint_as_float(rec_word(q, slot));
+  } else {
+    const unsigned wd = rec_word(q, slot >> 1);
+    return __ushort_as_bfloat16((unsigned short)((slot & 1) ? (wd >> 16) : (wd & 0xffffu)));
+  }
+}
+
+template <int W>
+struct Shared3 {
+  int wdone[W][kMaxWarpsPerPlane];  // per compute warp: all local steps < value are finished
+  int avail[kMaxWarpsPerPlane];     // previous CTA's last plane, per warp: global time finished
+  int abort;
+  int group;
+};
+
+// FP64 sweeps hold their operands in register pairs: they get at most 12
+// compute warps (ny <= 384) and the registers that leaves, 8 (ny <= 256)
+// when they use every stencil entry; FP32 / BF16 sweeps up to 16.
+template <int PK, int KIND>
+__host__ __device__ constexpr int max_threads() {
+  return PK == K64 ? (KIND == SW_GS_FULL ? 320 : 448) : kMaxThreads;
+}
+
+template <int PK, int NS, int KIND, int DIR, int W, int X, int REC>
+__global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Params P) {
+  using V = typename Prec<PK>::vec;
+  using Val = typename Prec<PK>::val;
+  using S = Shape<NS>;
+  constexpr int SA = S::SA, SB = S::SB, EC = S::EC;
+  constexpr bool SPLIT = REC && (KIND == SW_ILU_L || KIND == SW_ILU_U);
+  using R = IluRec<PK, NS, KIND == SW_ILU_U>;
+  // FOLD (FP64 / FP32): the sum of a point starts from b and subtracts its
+  // terms.  BF16 keeps b apart (the row scale multiplies the sum only).
+  constexpr bool FOLD = PK != KBF;
+  constexpr V sg = FOLD ? V(-1) : V(1);
+  constexpr bool NEED_D = KIND != SW_ILU_L;
+  extern __shared__ unsigned char dyn_smem[];
+  __shared__ Shared3<W> sh;
+
+  const Grid g = P.g;
+  const int NW = (g.ny + 31) >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ncompute = W * NW;  // warps ncompute and ncompute + 1 talk to the other CTAs
+  constexpr int LEAD = kRing - SB - 2;  // largest lead over the right-hand warp
+  // shared value ring: hist[plane][k % kRing][column]
+  V* hist = (V*)dyn_smem;
+  const int ngroups = (g.nx + W - 1) / W;
+
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      sh.group = atomicAdd(&P.ws->ticket, 1);
+      sh.abort = 0;
+    }
+    __syncthreads();
+    const int I = sh.group;
+    if (I >= ngroups) break;
+    const int nplanes = min(W, g.nx - I * W);
+    if (threadIdx.x < W * kMaxWarpsPerPlane) {
+      const int p = threadIdx.x / kMaxWarpsPerPlane, w = threadIdx.x % kMaxWarpsPerPlane;
+      // a warp has trivially finished every step before its first one
+      sh.wdone[p][w] = (p < nplanes && w < NW) ? SB * 32 * w - 2 : kDone;
+    }
+    // nothing precedes the first plane; 0 is below every time a later plane asks for
+    if (threadIdx.x < kMaxWarpsPerPlane) sh.avail[threadIdx.x] = (I == 0) ? kDone : 0;
+    __syncthreads();
+
+    if (warp == ncompute) {
+      // ---- publisher warp: lane w publishes the progress of warp w of the
+      // CTA's last plane with a GPU-scope release store whenever it grows
+      const int plast = nplanes - 1;
+      const int gt0 = SA * (I * W + plast);
+      const bool mine = lane < NW;
+      int* out_slot = P.ws->prog + (size_t)I * NW + lane;
+      int published = INT_MIN;
+      for (;;) {
+        const int T = mine ? ld_acq_cta(&sh.wdone[plast][lane]) : kDone;
+        if (__any_sync(0xffffffffu, mine && T != published)) {
+          // one release (one GPU-scope fence) covers every lane's value; a
+          // fence also stalls the SM's other memory traffic, so they are
+          // spaced by a fraction of a step
+          if (mine) st_release(out_slot, T >= kDone ? kDone : gt0 + T);
+          published = T;
+          if (__all_sync(0xffffffffu, T >= kDone)) break;
+          __nanosleep(kPublishGapNs);
+        } else {
+          __nanosleep(32);
+        }
+        if (__any_sync(0xffffffffu, ld_acq_cta(&sh.abort) != 0)) {
+          // release everything downstream; the error word is already set
+          if (mine) st_release(out_slot, kDone);
+          break;
+        }
+      }
+    } else if (warp == ncompute + 1) {
+      // ---- poller warp: lane w forwards the progress of warp w of the
+      // previous CTA's last plane into shared memory (GPU-scope acquire loads)
+      const bool mine = lane < NW;
+      const int* in_slot = P.ws->prog + (size_t)(I - 1) * NW + lane;
+      int seen = (I == 0 || !mine) ? kDone : 0;
+      unsigned long long t_wait = 0;
+      unsigned iter = 0;
+      while (__any_sync(0xffffffffu, seen < kDone)) {
+        int v = seen;
+        if (seen < kDone) asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(in_slot) : "memory");
+        const bool fresh = v > seen;
+        bool stop = false;
+        if (__any_sync(0xffffffffu, fresh)) {
+          if (fresh) {
+            seen = v;
+            st_rel_cta(&sh.avail[lane], v);
+          }
+          t_wait = 0;
+        } else if (lane == 0) {
+          // bounded: the previous CTA must make progress within the budget
+          const unsigned long long now = globaltimer_ns();
+          if (t_wait == 0) t_wait = now;
+          else if (now - t_wait > P.budget_ns) {
+            atomicCAS(P.err, 0, DEV_ERR_TIMEOUT);
+            stop = true;
+          }
+        }
+        if ((++iter & 63u) == 0 && lane == 0) stop = stop || ld_relaxed(P.err) != 0 || ld_acq_cta(&sh.abort) != 0;
+        if (__shfl_sync(0xffffffffu, stop, 0)) {
+          if (lane == 0) st_rel_cta(&sh.abort, 1);
+          break;
+        }
+      }
+    } else if (warp < W * NW) {
+      // ---- compute warp (p, w)
+      const int p = warp / NW, w = warp % NW;
+      if (p < nplanes) {
+        const V* b = (const V*)P.b;
+        V* u = (V*)P.u;
+        const V* __restrict__ dinv = (const V*)P.dinv;
+        const bool relax = P.w != 1.0;
+        const V wv = (V)P.w;
+        const int Ip = I * W + p;  // schedule plane
+        const int i = DIR > 0 ? Ip : g.nx - 1 - Ip;
+        const int J = 32 * w + lane;
+        const bool colok = J < g.ny;
+        const int j = DIR > 0 ? J : g.ny - 1 - J;
+        const int jlast = min(32 * w + 31, g.ny - 1);
+        const int s_begin = SB * 32 * w - 2;
+        const int s_end = SB * jlast + g.nz - 1;
+        const int gt0 = SA * Ip;
+        V* hp = hist + (size_t)p * kRing * (NW * 32);
+        int have_left = (w == 0) ? kDone : INT_MIN;        // cached progress of the left warp
+        int have_right = (w + 1 == NW) ? kDone : INT_MIN;  // cached progress of the right warp
+        int have_up = INT_MIN;                             // cached progress of the previous plane
+        const long long colbase = ((long long)i * g.ny + j) * g.nz;
+
+        // stage 2: operands of point K+2, loaded at step s, pre-summed at s+1
+        Val c2[NS];
+        V x2[NS];
+        V b2 = V(0), d2 = V(0), uo2 = V(0);
+        float s2 = 1.0f;
+        // finish operands of point K (pre-summed at s-1) and of point K+1
+        Val cfK[NS], cfN[NS];
+        V accK = V(0), bK = V(0), dK = V(0), uoK = V(0);
+        float sK = 1.0f;
+        V x1[NS];  // previous-plane terms of point K loaded one step ahead
+        V carry = V(0);
+#pragma unroll
+        for (int e = 0; e < NS; ++e) {
+          c2[e] = Val(0);
+          cfK[e] = cfN[e] = Val(0);
+          x2[e] = x1[e] = V(0);
+        }
+
+        // value of neighbour e of sweep point KK (grid index k of KK given)
+        auto nb = [&](int e, int kk) -> V {
+          const int ox = S::o(e, 0), oy = S::o(e, 1), oz = S::o(e, 2);
+          const bool in = (unsigned)(i + ox) < (unsigned)g.nx && (unsigned)(j + oy) < (unsigned)g.ny &&
+                          (unsigned)(kk + oz) < (unsigned)g.nz;
+          if (!in) return V(0);
+          const V* q = u + colbase + kk + P.lin[e];
+          // the previous schedule plane of another CTA: read through L2;
+          // everything else (this CTA's planes, old values) through L1
+          return ((DIR * ox < 0) && p == 0) ? __ldcg(q) : *q;
+        };
+
+        bool aborted = false;
+        for (int s = s_begin; s <= s_end; ++s) {
+          // -- dependencies, checked by lane 0 against cached counters
+          if (lane == 0) {
+            unsigned long long t_start = 0;
+            for (;;) {
+              bool ok = true;
+              if (have_left < s) {
+                have_left = ld_acq_cta(&sh.wdone[p][w - 1]);
+                ok = have_left >= s;
+              }
+              if (ok && have_right < s - LEAD) {
+                have_right = ld_acq_cta(&sh.wdone[p][w + 1]);
+                ok = have_right >= s - LEAD;
+              }
+              if (ok) {
+                // the previous plane's points this warp reads lie in columns
+                // 32w-1 .. 32w+32: warps w-1..w+1, SA + X steps ahead
+                const int need = (p == 0) ? gt0 + s + X : s + SA + X;
+                if (have_up < need) {
+                  const int* src = (p == 0) ? sh.avail : sh.wdone[p - 1];
+                  int T = kDone;
+                  for (int ww = max(w - 1, 0); ww <= min(w + 1, NW - 1); ++ww) T = min(T, ld_acq_cta(&src[ww]));
+                  have_up = T;
+                  ok = have_up >= need;
+                }
+              }
+              if (ok) break;
+              if (ld_acq_cta(&sh.abort)) { aborted = true; break; }
+              const unsigned long long now = globaltimer_ns();
+              if (t_start == 0) t_start = now;
+              else if (now - t_start > P.budget_ns) {
+                atomicCAS(P.err, 0, DEV_ERR_TIMEOUT);
+                st_rel_cta(&sh.abort, 1);
+                aborted = true;
+                break;
+              }
+            }
+          }
+          aborted = __shfl_sync(0xffffffffu, aborted, 0);
+          if (aborted) break;
+          __syncwarp();
+          const int K = s - SB * J;
+          const bool okK = colok && K >= 0 && K < g.nz;
+          const bool okK1 = colok && K + 1 >= 0 && K + 1 < g.nz;
+          const int kK = DIR > 0 ? K : g.nz - 1 - K;
+
+          // (a) previous-plane terms of K whose slack is one step: loaded now
+          V x0[NS];
+#pragma unroll
+          for (int e = 0; e < NS; ++e) {
+            x0[e] = V(0);
+            if (use<NS, KIND, DIR, X>(e) == U_FIN0 && okK) x0[e] = nb(e, kK);
+          }
+
+          // (b) pre-sum of point K+1: every term that is final by now
+          V accN = V(0), bN = V(0), dN = V(0), uoN = V(0);
+          float sN = 1.0f;
+          if (okK1) {
+            V a = FOLD ? b2 : V(0);
+#pragma unroll
+            for (int e = 0; e < NS; ++e) {
+              if (use<NS, KIND, DIR, X>(e) != U_PRE) continue;
+              V tv;
+              if (cls<NS, KIND, DIR>(e) == T_Y) {
+                const int kk = K + 1 + DIR * S::o(e, 2);  // sweep index of the left column's point
+                tv = (J > 0 && kk >= 0 && kk < g.nz) ? hp[(kk & (kRing - 1)) * (NW * 32) + J - 1] : V(0);
+              } else {
+                tv = x2[e];
+              }
+              a = fma(sg * (V)to_c(c2[e]), tv, a);
+            }
+            accN = a;
+            bN = b2;
+            dN = d2;
+            sN = s2;
+            uoN = uo2;
+          }
+#pragma unroll
+          for (int e = 0; e < NS; ++e) cfN[e] = c2[e];
+
+          // (c) finish point K
+          if (okK) {
+            V a = accK;
+#pragma unroll
+            for (int e = 0; e < NS; ++e) {
+              const int us = use<NS, KIND, DIR, X>(e);
+              if (us != U_FIN0 && us != U_FIN1 && us != U_FINR) continue;
+              V tv;
+              if (cls<NS, KIND, DIR>(e) == T_OWN) {
+                tv = carry;
+              } else if (cls<NS, KIND, DIR>(e) == T_Y) {
+                const int kk = K + DIR * S::o(e, 2);
+                tv = (J > 0 && kk >= 0 && kk < g.nz) ? hp[(kk & (kRing - 1)) * (NW * 32) + J - 1] : V(0);
+              } else {
+                tv = us == U_FIN0 ? x0[e] : x1[e];
+              }
+              a = fma(sg * (V)to_c(cfK[e]), tv, a);
+            }
+            if (PK == KBF) a = (V)sK * a;
+            V r;
+            if (KIND == SW_ILU_L) {
+              r = FOLD ? a : bK - a;
+            } else {
+              r = (FOLD ? a : bK - a) * dK;
+              if (KIND != SW_ILU_U && relax) r = (KIND == SW_GS_ZERO) ? wv * r : (V(1) - wv) * uoK + wv * r;
+            }
+            u[colbase + kK] = r;
+            hp[(K & (kRing - 1)) * (NW * 32) + J] = r;
+            carry = r;
+          }
+          // -- point K is stored: publish step s before the loads below are
+          // issued, so the release does not wait for them
+          __syncwarp();
+          if (lane == 0) st_rel_cta(&sh.wdone[p][w], s + 1);
+          accK = accN;
+          bK = bN;
+          dK = dN;
+          sK = sN;
+          uoK = uoN;
+#pragma unroll
+          for (int e = 0; e < NS; ++e) cfK[e] = cfN[e];
+
+          // (d) previous-plane terms of K+1 whose slack allows one step
+          if (okK1) {
+            const int k1 = DIR > 0 ? K + 1 : g.nz - 2 - K;
+#pragma unroll
+            for (int e = 0; e < NS; ++e)
+              if (use<NS, KIND, DIR, X>(e) == U_FIN1) x1[e] = nb(e, k1);
+          }
+
+          // (e) operands of point K+2
+          const int K2 = K + 2;
+          if (colok && K2 >= 0 && K2 < g.nz) {
+            const int k2 = DIR > 0 ? K2 : g.nz - 1 - K2;
+            const long long p2 = colbase + k2;
+            if (SPLIT) {
+              uint4 q[R::CHUNKS];
+              const uint4* rp = (const uint4*)((const char*)P.M + p2 * R::BYTES);
+#pragma unroll
+              for (int c = 0; c < R::CHUNKS; ++c) q[c] = __ldg(rp + c);
+#pragma unroll
+              for (int e = 0; e < NS; ++e) {
+                if (use<NS, KIND, DIR, X>(e) == U_NONE) continue;
+                c2[e] = rec_val<Val>(q, KIND == SW_ILU_L ? e : e - EC - 1);
+              }
+              if (R::HAS_D) d2 = (V)rec_val<Val>(q, R::D_OFF / (int)sizeof(Val));
+              if (R::HAS_S) s2 = __uint_as_float(rec_word(q, R::S_OFF / 4));
+              if (KIND == SW_ILU_U && !R::HAS_D) d2 = dinv[p2];
+            } else {
+              const Val* __restrict__ a = (const Val*)P.M + p2 * NS;
+#pragma unroll
+              for (int e = 0; e < NS; ++e)
+                if (use<NS, KIND, DIR, X>(e) != U_NONE) c2[e] = a[e];
+              if (NEED_D) d2 = dinv[p2];
+              if (PK == KBF) s2 = P.scale[p2];
+            }
+#pragma unroll
+            for (int e = 0; e < NS; ++e)
+              if (use<NS, KIND, DIR, X>(e) == U_PRE && cls<NS, KIND, DIR>(e) != T_Y) x2[e] = nb(e, k2);
+            b2 = b[p2];
+            if (KIND == SW_GS_FULL && relax) uo2 = u[p2];
+            if (K2 + kPrefetch < g.nz) {
+              constexpr int RB = SPLIT ? R::BYTES : NS * (int)sizeof(Val);
+              const char* pf = (const char*)P.M + (p2 + DIR * kPrefetch) * RB;
+              prefetch_l2(pf);
+              prefetch_l2(pf + RB - 1);
+            }
+          }
+        }
+        if (lane == 0) st_rel_cta(&sh.wdone[p][w], kDone);
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    sh.group = (atomicAdd(&P.ws->finished, 1) == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  if (sh.group) {
+    for (int q = threadIdx.x; q < ngroups * NW; q += blockDim.x) P.ws->prog[q] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      P.ws->ticket = 0;
+      __threadfence();
+      P.ws->finished = 0;
+    }
+  }
+}
+
+template <int NS>
+bool canonical(const Stencil& s) {
+  if (s.ns != NS) return false;
+  for (int e = 0; e < NS; ++e)
+    for (int d = 0; d < 3; ++d)
+      if (s.off[e][d] != Shape<NS>::o(e, d)) return false;
+  return true;
+}
+
+template <int PK, int NS, int W, int X>
+cudaError_t launch_kind(int kind, int dir, bool rec, const Sweep3Params& P, cudaStream_t st) {
+  using V = typename Prec<PK>::vec;
+  const int NW = (P.g.ny + 31) / 32;
+  const int nthr = (W * NW + 2) * 32;
+  // the value ring needs <= 64 KB (ny <= 512); reserving more than half of
+  // the SM's 228 KB keeps a second CTA off the SM
+  const size_t smem = std::max(sizeof(V) * kRing * (size_t)(NW * 32) * W, kOneCtaPerSmSmem);
+  int dev = 0, nsm = 0;
+  cudaError_t ae = cudaGetDevice(&dev);
+  if (ae == cudaSuccess) ae = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (ae != cudaSuccess) return ae;
+  const int grid = std::min((P.g.nx + W - 1) / W, nsm);
+  auto go = [&](auto kern) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, nthr, smem, st>>>(P);
+    return cudaGetLastError();
+  };
+  if (kind == SW_GS_ZERO) return go(k_sweep3<PK, NS, SW_GS_ZERO, 1, W, X, 0>);
+  if (kind == SW_GS_FULL) {
+    if (dir > 0) return go(k_sweep3<PK, NS, SW_GS_FULL, 1, W, X, 0>);
+    return go(k_sweep3<PK, NS, SW_GS_FULL, -1, W, X, 0>);
+  }
+  if constexpr (PK == K64) {
+    // the unsplit factors are read only by the context-free entry point (FP64)
+    if (!rec) {
+      if (kind == SW_ILU_L) return go(k_sweep3<PK, NS, SW_ILU_L, 1, W, X, 0>);
+      return go(k_sweep3<PK, NS, SW_ILU_U, -1, W, X, 0>);
+    }
+  } else {
+    if (!rec) return cudaErrorNotSupported;
+  }
+  if (kind == SW_ILU_L) return go(k_sweep3<PK, NS, SW_ILU_L, 1, W, X, 1>);
+  return go(k_sweep3<PK, NS, SW_ILU_U, -1, W, X, 1>);
+}
+
+}  // namespace sweep3
+
+// One entry per working precision, each compiled in its own translation unit.
+cudaError_t sweep3_launch_k64(int ns, int kind, int dir, bool rec, const sweep3::Sweep3Params& P, cudaStream_t st);
+cudaError_t sweep3_launch_k32(int ns, int W, int kind, int dir, bool rec, const sweep3::Sweep3Params& P,
+                              cudaStream_t st);
+cudaError_t sweep3_launch_kbf(int ns, int W, int kind, int dir, bool rec, const sweep3::Sweep3Params& P,
+                              cudaStream_t st);

@@ -70,6 +70,8 @@ def lib():
         L.smg_version.restype = ctypes.c_char_p
         L.smg_launch_count.restype = ctypes.c_longlong
         L.smg_selftest_wait.argtypes = [vp, i, vp]
+        L.smg_set_wait_budget_ns.argtypes = [vp, ctypes.c_longlong]
+        L.smg_vcycle_profile.argtypes = [vp, vp, vp, i, ip, ip, ip, ctypes.POINTER(ctypes.c_float), vp]
         L.smg_sweep_noalloc.argtypes = [i, ip, i, ip, vp, vp, vp, vp, d, i, vp]
         sz = ctypes.c_size_t
         f = ctypes.c_float
@@ -124,6 +126,14 @@ def sweep_noalloc(op, dims, offsets, M, dinv, b, u, relax_w=1.0, spin_budget_ms=
     """One GS or ILU(0) sweep through smg_sweep_noalloc, the entry point that
     allocates no device memory (for callers whose device memory is owned by
     someone else).  Tensors are float64 CUDA tensors; returns the status."""
+    import torch
+    n = int(dims[0]) * int(dims[1]) * int(dims[2])
+    for name, t, count in (("M", M, n * len(offsets)), ("dinv", dinv, n), ("b", b, n), ("u", u, n)):
+        if t is None:
+            continue  # passed as NULL: the library decides whether the op needs it
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != count:
+            raise ValueError("sweep_noalloc: %s must be a contiguous float64 CUDA tensor of %d values, got %s %s "
+                             "with %d values" % (name, count, t.dtype, t.device, t.numel()))
     flat = [c for o in offsets for c in o]
     return lib().smg_sweep_noalloc(op, _iarr(dims), len(offsets), _iarr(flat), _ptr(M), _ptr(dinv), _ptr(b),
                                    _ptr(u), relax_w, spin_budget_ms, _stream(stream))
@@ -285,6 +295,28 @@ class SMG:
                                              _ptr(loss), _ptr(ws), ws.numel(), _stream(stream))
         if rc != OK:
             raise SmgError(rc, "smg_learned_loss_grad")
+
+    STAGES = {1: "pre1", 2: "pre2", 3: "residual", 4: "restrict", 5: "coarse", 6: "prolong", 7: "post_residual",
+              8: "post1", 9: "post2", 10: "post_add", 11: "cast", 12: "learned"}
+
+    def vcycle_profile(self, r, z, stream=None):
+        """One eager V-cycle with an event after every stage; returns a list of
+        (level, stage name, device ms)."""
+        cap = 512
+        cnt = ctypes.c_int()
+        lv, sg = (ctypes.c_int * cap)(), (ctypes.c_int * cap)()
+        ms = (ctypes.c_float * cap)()
+        rc = self._lib.smg_vcycle_profile(self.h, _ptr(r), _ptr(z), cap, ctypes.byref(cnt), lv, sg, ms,
+                                          _stream(stream))
+        if rc != OK:
+            raise SmgError(rc, "smg_vcycle_profile")
+        return [(lv[t], self.STAGES.get(sg[t], str(sg[t])), float(ms[t])) for t in range(min(cnt.value, cap))]
+
+    def set_wait_budget_ns(self, budget_ns):
+        """Bound of every device wait of this context, in ns (0: give up at once)."""
+        rc = self._lib.smg_set_wait_budget_ns(self.h, int(budget_ns))
+        if rc != OK:
+            raise SmgError(rc, "smg_set_wait_budget_ns")
 
     def selftest_wait(self, budget_ms=20, stream=None):
         """Runs one bounded device wait that must time out; returns the status."""

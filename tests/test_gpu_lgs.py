@@ -180,3 +180,28 @@ def test_lgs_vcycle_graph_replay_and_determinism(S):
     hg.vcycle(r, z2)
     hg.vcycle(r, z3)
     assert torch.equal(z1, z2) and torch.equal(z2, z3)
+
+
+def test_lgs_abort_path_drains_and_the_context_survives(S, orc):
+    """With a zero wait budget, every dependency wait of the line sweep that
+    is not satisfied at once gives up: the sweep takes its abort path, which
+    must drain the column copies it issued.  With the budget restored the same
+    context then sweeps exactly as the oracle, twice in a row."""
+    d = (8, 12, 64)  # even nz: the column data are staged by bulk copies; n <= 8192 (one level)
+    off, A = problem("q1z", d)
+    n = int(np.prod(d))
+    h = S.SMG(d, off, cu(A), smoother=S.LGS, max_levels=1)
+    b = cu(I.rhs(n, 5).numpy())
+    h.set_wait_budget_ns(0)
+    status = S.OK
+    try:
+        h.level_apply(0, S.OP_LGS_FORWARD, x=torch.zeros_like(b), b=b)
+    except S.SmgError as e:
+        status = e.status
+    assert status in (S.OK, S.ETIMEOUT)
+    h.set_wait_budget_ns(10 ** 9)
+    ref = orc.lgs_forward(d, off, A, host(b), np.zeros(n))
+    for _ in range(2):
+        x = torch.zeros_like(b)
+        h.level_apply(0, S.OP_LGS_FORWARD, x=x, b=b)
+        assert rel_max(host(x), ref) < TOL_SWEEP

@@ -528,3 +528,29 @@ def test_launch_counter_counts_kernels(S):
     hg.vcycle(r, z)
     hg.vcycle(r, z)
     assert S.launch_count() - c0 == 2 * per
+
+
+@pytest.mark.parametrize("smoother", ["ilu", "sgs"])
+def test_zero_wait_budget_aborts_and_context_survives(S, orc, smoother):
+    """A zero wait budget makes the wavefront sweeps give up at their first
+    unsatisfied wait (error word set, every CTA drains); with the budget
+    restored the same context runs a V-cycle equal to the oracle's."""
+    d = (24, 40, 24)
+    off, A = problem("q1", d)
+    n = int(np.prod(d))
+    sm = S.ILU0 if smoother == "ilu" else S.SGS
+    h = make(S, d, off, A, smoother=sm)
+    r = cu(I.rhs(n, 2).numpy())
+    z = torch.empty_like(r)
+    h.set_wait_budget_ns(0)
+    status = S.OK
+    try:
+        h.vcycle(r, z)
+    except S.SmgError as e:
+        status = e.status
+    assert status in (S.OK, S.ETIMEOUT)
+    h.set_wait_budget_ns(10 ** 9)
+    ref = orc.MG(d, off, A, smoother=orc.ILU0 if smoother == "ilu" else orc.SGS).vcycle(host(r))
+    for _ in range(2):
+        h.vcycle(r, z)
+        assert rel2(host(z), ref) < TOL_VCYCLE
