@@ -395,35 +395,97 @@ __global__ void k_lower(Grid g, Stencil s, const double* __restrict__ A, int pk,
   for (int e = 0; e < s.ns; ++e) v[e] = __double2bfloat16(a[e] / (double)(e < s.ec ? sl : su));
 }
 
-// Split ILU(0) records (ilurec.cuh) of every point, from the FP64 factors.
-// The values and scales equal those of k_lower(split = 1) entry by entry.
+// Sweep records (ilurec.cuh) of every point, from the FP64 ILU factors or
+// matrix, written in the skewed layout.  Values and scales equal those of
+// k_lower entry by entry (split = 1 for the ILU triangles, 0 for the matrix).
+template <typename R>
+struct RecBuf {
+  union {
+    uint4 q[R::CHUNKS];
+    unsigned char b[R::BYTES];
+  };
+};
+
+__device__ __forceinline__ void grid_ijk(const Grid& g, long long p, int& i, int& j, int& k) {
+  k = (int)(p % g.nz);
+  j = (int)((p / g.nz) % g.ny);
+  i = (int)(p / ((long long)g.ny * g.nz));
+}
+
 template <int PK, int NS>
-__global__ void k_ilu_split(Grid g, const double* __restrict__ LU, const double* __restrict__ udinv, void* Lrec,
-                            void* Urec) {
+__global__ void k_ilu_records(Grid g, int SB, const double* __restrict__ LU, const double* __restrict__ udinv,
+                              uint4* __restrict__ Lrec, uint4* __restrict__ Urec) {
   using Val = typename Prec<PK>::val;
-  using RL = IluRec<PK, NS, false>;
-  using RU = IluRec<PK, NS, true>;
+  using Vec = typename Prec<PK>::vec;
+  using RL = SweepRec<PK, NS, 0>;
+  using RU = SweepRec<PK, NS, 1>;
   constexpr int EC = Shape<NS>::EC;
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= g.n) return;
   const double* a = LU + p * NS;
-  unsigned char* lr = (unsigned char*)Lrec + p * RL::BYTES;
-  unsigned char* ur = (unsigned char*)Urec + p * RU::BYTES;
-  for (int t = 0; t < RL::CHUNKS; ++t) ((uint4*)lr)[t] = make_uint4(0, 0, 0, 0);
-  for (int t = 0; t < RU::CHUNKS; ++t) ((uint4*)ur)[t] = make_uint4(0, 0, 0, 0);
-  Val* lv = (Val*)lr;
-  Val* uv = (Val*)ur;
+  RecBuf<RL> L;
+  RecBuf<RU> U;
+  for (int c = 0; c < RL::CHUNKS; ++c) L.q[c] = make_uint4(0, 0, 0, 0);
+  for (int c = 0; c < RU::CHUNKS; ++c) U.q[c] = make_uint4(0, 0, 0, 0);
+  Val* lv = (Val*)L.b;
+  Val* uv = (Val*)U.b;
   if constexpr (PK == KBF) {
     const float sl = row_scale(a, 0, EC), su = row_scale(a, EC + 1, NS);
     for (int e = 0; e < EC; ++e) lv[e] = __double2bfloat16(a[e] / (double)sl);
-    for (int e = EC + 1; e < NS; ++e) uv[e - EC - 1] = __double2bfloat16(a[e] / (double)su);
-    *(float*)(lr + RL::S_OFF) = sl;
-    *(float*)(ur + RU::S_OFF) = su;
+    for (int e = EC + 1; e < NS; ++e) uv[RU::slot(e)] = __double2bfloat16(a[e] / (double)su);
+    *(float*)(L.b + RL::S_OFF) = sl;
+    *(float*)(U.b + RU::S_OFF) = su;
   } else {
     for (int e = 0; e < EC; ++e) lv[e] = (Val)a[e];
-    for (int e = EC + 1; e < NS; ++e) uv[e - EC - 1] = (Val)a[e];
-    *(Val*)(ur + RU::D_OFF) = (Val)udinv[p];
+    for (int e = EC + 1; e < NS; ++e) uv[RU::slot(e)] = (Val)a[e];
   }
+  *(Vec*)(U.b + RU::D_OFF) = (Vec)udinv[p];
+  int i, j, k;
+  grid_ijk(g, p, i, j, k);
+  const long long row = (long long)i * g.nz + skew_row(j, k, SB, g.nz);
+  for (int c = 0; c < RL::CHUNKS; ++c) Lrec[(row * RL::CHUNKS + c) * g.ny + j] = L.q[c];
+  for (int c = 0; c < RU::CHUNKS; ++c) Urec[(row * RU::CHUNKS + c) * g.ny + j] = U.q[c];
+}
+
+template <int PK, int NS>
+__global__ void k_gs_records(Grid g, int SB, const double* __restrict__ A, const double* __restrict__ dinv,
+                             uint4* __restrict__ Grec) {
+  using Val = typename Prec<PK>::val;
+  using Vec = typename Prec<PK>::vec;
+  using RG = SweepRec<PK, NS, 2>;
+  constexpr int EC = Shape<NS>::EC;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.n) return;
+  const double* a = A + p * NS;
+  RecBuf<RG> G;
+  for (int c = 0; c < RG::CHUNKS; ++c) G.q[c] = make_uint4(0, 0, 0, 0);
+  Val* v = (Val*)G.b;
+  if constexpr (PK == KBF) {
+    const float sc = row_scale(a, 0, NS);
+    for (int e = 0; e < NS; ++e)
+      if (e != EC) v[e] = __double2bfloat16(a[e] / (double)sc);
+    *(float*)(G.b + RG::S_OFF) = sc;
+  } else {
+    for (int e = 0; e < NS; ++e)
+      if (e != EC) v[e] = (Val)a[e];
+  }
+  *(Vec*)(G.b + RG::D_OFF) = (Vec)dinv[p];
+  int i, j, k;
+  grid_ijk(g, p, i, j, k);
+  const long long row = (long long)i * g.nz + skew_row(j, k, SB, g.nz);
+  for (int c = 0; c < RG::CHUNKS; ++c) Grec[(row * RG::CHUNKS + c) * g.ny + j] = G.q[c];
+}
+
+// Vector between natural order and the skewed layout.
+template <typename T>
+__global__ void k_skew_copy(Grid g, int SB, int to_skew, const T* __restrict__ src, T* __restrict__ dst, int add) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.n) return;
+  int i, j, k;
+  grid_ijk(g, p, i, j, k);
+  const long long q = skew_slot(g, SB, i, j, k);
+  if (to_skew) dst[q] = src[p];
+  else dst[p] = add ? dst[p] + src[q] : src[q];
 }
 
 // Stencil entries reordered: out[p][e] = in[p][perm[e]] (BxB blocks).
@@ -701,21 +763,47 @@ cudaError_t launch_lower_matrix(Grid g, const Stencil& s, const double* A, int p
   return cudaGetLastError();
 }
 
-cudaError_t launch_ilu_split(Grid g, int ns, int pk, const double* LU, const double* udinv, void* Lrec, void* Urec,
+cudaError_t launch_ilu_records(Grid g, int ns, int SB, int pk, const double* LU, const double* udinv, void* Lrec,
+                               void* Urec, cudaStream_t st) {
+  const int nb = div_up(g.n, TPB);
+  uint4 *l = (uint4*)Lrec, *u = (uint4*)Urec;
+#define REC_(PK, NS) k_ilu_records<PK, NS><<<nb, TPB, 0, st>>>(g, SB, LU, udinv, l, u)
+  if (ns != 7 && ns != 19 && ns != 27) return cudaErrorInvalidValue;
+  if (pk == K64) {
+    if (ns == 27) REC_(K64, 27); else if (ns == 19) REC_(K64, 19); else REC_(K64, 7);
+  } else if (pk == K32) {
+    if (ns == 27) REC_(K32, 27); else if (ns == 19) REC_(K32, 19); else REC_(K32, 7);
+  } else {
+    if (ns == 27) REC_(KBF, 27); else if (ns == 19) REC_(KBF, 19); else REC_(KBF, 7);
+  }
+#undef REC_
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gs_records(Grid g, int ns, int SB, int pk, const double* A, const double* dinv, void* Grec,
+                              cudaStream_t st) {
+  const int nb = div_up(g.n, TPB);
+  uint4* r = (uint4*)Grec;
+#define REC_(PK, NS) k_gs_records<PK, NS><<<nb, TPB, 0, st>>>(g, SB, A, dinv, r)
+  if (ns != 7 && ns != 19 && ns != 27) return cudaErrorInvalidValue;
+  if (pk == K64) {
+    if (ns == 27) REC_(K64, 27); else if (ns == 19) REC_(K64, 19); else REC_(K64, 7);
+  } else if (pk == K32) {
+    if (ns == 27) REC_(K32, 27); else if (ns == 19) REC_(K32, 19); else REC_(K32, 7);
+  } else {
+    if (ns == 27) REC_(KBF, 27); else if (ns == 19) REC_(KBF, 19); else REC_(KBF, 7);
+  }
+#undef REC_
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_skew_copy(Grid g, int SB, int vb, bool to_skew, const void* src, void* dst, bool add,
                              cudaStream_t st) {
   const int nb = div_up(g.n, TPB);
-#define SPLIT_(PK, NS) k_ilu_split<PK, NS><<<nb, TPB, 0, st>>>(g, LU, udinv, Lrec, Urec)
-  if (pk == K64) {
-    if (ns == 27) SPLIT_(K64, 27); else if (ns == 19) SPLIT_(K64, 19); else if (ns == 7) SPLIT_(K64, 7);
-    else return cudaErrorInvalidValue;
-  } else if (pk == K32) {
-    if (ns == 27) SPLIT_(K32, 27); else if (ns == 19) SPLIT_(K32, 19); else if (ns == 7) SPLIT_(K32, 7);
-    else return cudaErrorInvalidValue;
-  } else {
-    if (ns == 27) SPLIT_(KBF, 27); else if (ns == 19) SPLIT_(KBF, 19); else if (ns == 7) SPLIT_(KBF, 7);
-    else return cudaErrorInvalidValue;
-  }
-#undef SPLIT_
+  if (vb == 8) k_skew_copy<double><<<nb, TPB, 0, st>>>(g, SB, to_skew, (const double*)src, (double*)dst, add);
+  else k_skew_copy<float><<<nb, TPB, 0, st>>>(g, SB, to_skew, (const float*)src, (float*)dst, add);
   smg_count_launch(1);
   return cudaGetLastError();
 }

@@ -36,8 +36,9 @@ bool sweep3_supported(const LevelView& L, int kind) {
 // Planes per CTA: FP64 sweeps are bound by the FP64 pipe, so one plane per
 // CTA keeps the per-SM work at one plane; FP32 / BF16 sweeps are bound by
 // synchronisation latency, so two planes share a CTA and every other plane
-// hand-off stays inside the SM.  rec: the ILU operand M is split records
-// (ilurec.cuh) rather than the factors [n][NS].
+// hand-off stays inside the SM.  rec: M is the sweep's records and b, u are
+// vectors, all in the skewed layout (ilurec.cuh); otherwise M is the matrix
+// or ILU factors [n][NS] and the vectors are in natural order (FP64 only).
 cudaError_t launch_sweep3(const LevelView& L, int kind, int dir, const void* M, const float* sc1, const float* sc2,
                           const void* dinv, double w, const void* b, void* u, SweepWs* ws, int* err,
                           const SweepCfg& cfg, cudaStream_t st, bool rec) {

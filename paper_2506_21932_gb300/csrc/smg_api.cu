@@ -74,8 +74,13 @@ struct Level {
   SweepCfg cfg{};
   int* ilu_upd = nullptr;
   double* lf = nullptr;     // line Gauss-Seidel: per-column factors
-  void* Lrec = nullptr;     // ILU(0): split L / U records of the working precision (ilurec.cuh)
-  void* Urec = nullptr;
+  // warp-pipelined sweeps (canonical masks): records of the working
+  // precision in the skewed layout (ilurec.cuh) and two skewed vectors
+  void* Lrec = nullptr;     // ILU(0) lower solve
+  void* Urec = nullptr;     // ILU(0) upper solve
+  void* Grec = nullptr;     // Gauss-Seidel
+  void* vs0 = nullptr;
+  void* vs1 = nullptr;
 };
 
 struct smg_ctx {
@@ -224,12 +229,6 @@ static int sweep(smg_ctx* h, Level& L, int kind, int dir, const void* b, void* u
   const void* M;
   const float *s1 = nullptr, *s2 = nullptr;
   const void* dv;
-  if ((kind == SW_ILU_L || kind == SW_ILU_U) && L.Lrec) {
-    SMG_CUDA_TRY(launch_sweep3(v, kind, dir, kind == SW_ILU_L ? L.Lrec : L.Urec, nullptr, nullptr,
-                               lp ? L.dinv32 : (const void*)L.udinv, h->opt.relax_w, b, u, L.ws, h->err, L.cfg, st,
-                               true));
-    return SMG_OK;
-  }
   if (kind == SW_ILU_L || kind == SW_ILU_U) {
     M = lp ? L.LUv : (const void*)L.LU;
     s1 = L.Ls;
@@ -244,6 +243,23 @@ static int sweep(smg_ctx* h, Level& L, int kind, int dir, const void* b, void* u
   return SMG_OK;
 }
 
+// Levels whose sweeps run on the records and vectors of the skewed layout.
+static bool skewed(const Level& L) { return L.Lrec || L.Grec; }
+
+// One sweep of a skewed level; b and u are skewed vectors.
+static int sweep_rec(smg_ctx* h, Level& L, int kind, int dir, const void* b, void* u, cudaStream_t st) {
+  const void* M = kind == SW_ILU_L ? L.Lrec : (kind == SW_ILU_U ? L.Urec : L.Grec);
+  SMG_CUDA_TRY(launch_sweep3(view(h, L, true), kind, dir, M, nullptr, nullptr, nullptr, h->opt.relax_w, b, u, L.ws,
+                             h->err, L.cfg, st, true));
+  return SMG_OK;
+}
+
+// Vector between natural order and the level's skewed layout.
+static int skew(smg_ctx* h, Level& L, const void* src, void* dst, bool to_skew, bool add, cudaStream_t st) {
+  SMG_CUDA_TRY(launch_skew_copy(L.g, L.cfg.SB, (int)vsize(h), to_skew, src, dst, add, st));
+  return SMG_OK;
+}
+
 // One line Gauss-Seidel sweep (FP64 hierarchy only).
 static int lsweep(smg_ctx* h, Level& L, int kind, int dir, const void* b, void* u, cudaStream_t st) {
   SMG_CUDA_TRY(launch_lsweep(L.g, L.s, kind, dir, L.A, L.lf, (const double*)b, (double*)u, L.ws, h->err,
@@ -252,6 +268,17 @@ static int lsweep(smg_ctx* h, Level& L, int kind, int dir, const void* b, void* 
 }
 
 static int smooth_pre(smg_ctx* h, Level& L, int l, const void* f, void* u, cudaStream_t st) {
+  if (skewed(L)) {
+    // f -> vs0; the first sweep writes vs1 from zero, the second updates it
+    TRY(skew(h, L, f, L.vs0, true, false, st));
+    const bool ilu = h->opt.smoother == SMG_SMOOTHER_ILU0;
+    TRY(sweep_rec(h, L, ilu ? SW_ILU_L : SW_GS_ZERO, +1, L.vs0, L.vs1, st));
+    prof_mark(h, l, PM_PRE1, st);
+    TRY(sweep_rec(h, L, ilu ? SW_ILU_U : SW_GS_FULL, -1, ilu ? L.vs1 : L.vs0, L.vs1, st));
+    TRY(skew(h, L, L.vs1, u, false, false, st));
+    prof_mark(h, l, PM_PRE2, st);
+    return SMG_OK;
+  }
   if (h->opt.smoother == SMG_SMOOTHER_LGS) {
     TRY(lsweep(h, L, SW_GS_ZERO, +1, f, u, st));
     prof_mark(h, l, PM_PRE1, st);
@@ -270,6 +297,30 @@ static int smooth_pre(smg_ctx* h, Level& L, int l, const void* f, void* u, cudaS
 }
 
 static int smooth_post(smg_ctx* h, Level& L, int l, const void* f, void* u, cudaStream_t st) {
+  if (skewed(L)) {
+    if (h->opt.smoother == SMG_SMOOTHER_ILU0) {
+      // u += U^-1 L^-1 (f - A u): the residual in natural order, the solves
+      // on skewed vectors, the correction added while unpacking
+      SMG_CUDA_TRY(launch_spmv(view(h, L, true), u, f, L.t, 1, st));
+      TRY(skew(h, L, L.t, L.vs0, true, false, st));
+      prof_mark(h, l, PM_POST_RESID, st);
+      TRY(sweep_rec(h, L, SW_ILU_L, +1, L.vs0, L.vs1, st));
+      prof_mark(h, l, PM_POST1, st);
+      TRY(sweep_rec(h, L, SW_ILU_U, -1, L.vs1, L.vs1, st));
+      prof_mark(h, l, PM_POST2, st);
+      TRY(skew(h, L, L.vs1, u, false, true, st));
+      prof_mark(h, l, PM_POST_ADD, st);
+    } else {
+      TRY(skew(h, L, f, L.vs0, true, false, st));
+      TRY(skew(h, L, u, L.vs1, true, false, st));
+      TRY(sweep_rec(h, L, SW_GS_FULL, +1, L.vs0, L.vs1, st));
+      prof_mark(h, l, PM_POST1, st);
+      TRY(sweep_rec(h, L, SW_GS_FULL, -1, L.vs0, L.vs1, st));
+      TRY(skew(h, L, L.vs1, u, false, false, st));
+      prof_mark(h, l, PM_POST2, st);
+    }
+    return SMG_OK;
+  }
   if (h->opt.smoother == SMG_SMOOTHER_LGS) {
     TRY(lsweep(h, L, SW_GS_FULL, +1, f, u, st));
     prof_mark(h, l, PM_POST1, st);
@@ -521,11 +572,23 @@ static int setup_level_smoother(smg_ctx* h, Level& L, cudaStream_t st) {
       SMG_CUDA_TRY(launch_d2f_array(L.udinv, (float*)L.dinv32, n, st));
     }
   }
-  // ILU(0) triangular solves on the warp-pipelined kernel read split records
-  if (h->opt.smoother == SMG_SMOOTHER_ILU0 && sweep3_supported(view(h, L, true), SW_ILU_L)) {
-    TRY(dev_alloc(h, &L.Lrec, (size_t)n * ilu_rec_bytes(h->pk, L.s.ns, false)));
-    TRY(dev_alloc(h, &L.Urec, (size_t)n * ilu_rec_bytes(h->pk, L.s.ns, true)));
-    SMG_CUDA_TRY(launch_ilu_split(L.g, L.s.ns, h->pk, L.LU, L.udinv, L.Lrec, L.Urec, st));
+  // point smoothers on the warp-pipelined kernel read records of the skewed
+  // layout (ilurec.cuh), on skewed vectors
+  const bool ilu = h->opt.smoother == SMG_SMOOTHER_ILU0, sgs = h->opt.smoother == SMG_SMOOTHER_SGS;
+  const LevelView lv = view(h, L, true);
+  if (B == 1 && ((ilu && sweep3_supported(lv, SW_ILU_L)) ||
+                 (sgs && sweep3_supported(lv, SW_GS_ZERO) && sweep3_supported(lv, SW_GS_FULL)))) {
+    const size_t unit = 16 * (size_t)n;
+    if (ilu) {
+      TRY(dev_alloc(h, &L.Lrec, unit * sweep_rec_chunks(h->pk, L.s.ns, 0)));
+      TRY(dev_alloc(h, &L.Urec, unit * sweep_rec_chunks(h->pk, L.s.ns, 1)));
+      SMG_CUDA_TRY(launch_ilu_records(L.g, L.s.ns, L.cfg.SB, h->pk, L.LU, L.udinv, L.Lrec, L.Urec, st));
+    } else {
+      TRY(dev_alloc(h, &L.Grec, unit * sweep_rec_chunks(h->pk, L.s.ns, 2)));
+      SMG_CUDA_TRY(launch_gs_records(L.g, L.s.ns, L.cfg.SB, h->pk, L.A, L.dinv, L.Grec, st));
+    }
+    TRY(dev_alloc(h, &L.vs0, (size_t)n * vsize(h)));
+    TRY(dev_alloc(h, &L.vs1, (size_t)n * vsize(h)));
   }
   return SMG_OK;
 }
@@ -1032,6 +1095,14 @@ extern "C" int smg_level_apply(smg_t h, int l, int op, const void* x, const void
     case SMG_OP_GS_BACKWARD:
     case SMG_OP_GS_ZERO:
       if (!has_sm || h->opt.smoother != SMG_SMOOTHER_SGS || !x || !b) return SMG_EINVAL;
+      if (skewed(L)) {
+        TRY(skew(h, L, b, L.vs0, true, false, st));
+        if (op != SMG_OP_GS_ZERO) TRY(skew(h, L, x, L.vs1, true, false, st));
+        TRY(sweep_rec(h, L, op == SMG_OP_GS_ZERO ? SW_GS_ZERO : SW_GS_FULL, op == SMG_OP_GS_BACKWARD ? -1 : +1,
+                      L.vs0, L.vs1, st));
+        TRY(skew(h, L, L.vs1, (void*)x, false, false, st));
+        break;
+      }
       TRY(sweep(h, L, op == SMG_OP_GS_ZERO ? SW_GS_ZERO : SW_GS_FULL, op == SMG_OP_GS_BACKWARD ? -1 : +1, b,
                 (void*)x, st));
       break;
@@ -1044,6 +1115,13 @@ extern "C" int smg_level_apply(smg_t h, int l, int op, const void* x, const void
       break;
     case SMG_OP_ILU_APPLY:
       if (!has_sm || h->opt.smoother != SMG_SMOOTHER_ILU0 || !b || !y) return SMG_EINVAL;
+      if (skewed(L)) {
+        TRY(skew(h, L, b, L.vs0, true, false, st));
+        TRY(sweep_rec(h, L, SW_ILU_L, +1, L.vs0, L.vs1, st));
+        TRY(sweep_rec(h, L, SW_ILU_U, -1, L.vs1, L.vs1, st));
+        TRY(skew(h, L, L.vs1, y, false, false, st));
+        break;
+      }
       TRY(sweep(h, L, SW_ILU_L, +1, b, y, st));
       TRY(sweep(h, L, SW_ILU_U, -1, y, y, st));
       break;
@@ -1062,6 +1140,13 @@ extern "C" int smg_level_apply(smg_t h, int l, int op, const void* x, const void
     case SMG_OP_ILU_LOWER:
     case SMG_OP_ILU_UPPER:
       if (!has_sm || h->opt.smoother != SMG_SMOOTHER_ILU0 || !b || !y) return SMG_EINVAL;
+      if (skewed(L)) {
+        TRY(skew(h, L, b, L.vs0, true, false, st));
+        TRY(sweep_rec(h, L, op == SMG_OP_ILU_LOWER ? SW_ILU_L : SW_ILU_U, op == SMG_OP_ILU_LOWER ? +1 : -1, L.vs0,
+                      L.vs1, st));
+        TRY(skew(h, L, L.vs1, y, false, false, st));
+        break;
+      }
       TRY(sweep(h, L, op == SMG_OP_ILU_LOWER ? SW_ILU_L : SW_ILU_U, op == SMG_OP_ILU_LOWER ? +1 : -1, b, y, st));
       break;
     default:

@@ -178,9 +178,10 @@ cudaError_t launch_sweep2(const LevelView& L, int kind, int dir, const void* M, 
 
 // Warp-pipelined variant (same masks, ny <= 512): per-warp time loops synced
 // through shared-memory counters, a communication warp for the GPU-scope
-// hand-off; returns cudaErrorNotSupported when it does not apply.  rec: the
-// ILU operand M is the split L / U records of ilurec.cuh (FP32 / BF16 ILU
-// solves exist only in that form) instead of the factors [n][ns].
+// hand-off; returns cudaErrorNotSupported when it does not apply.  rec: M is
+// the sweep's records and b, u are vectors, all in the skewed layout of
+// ilurec.cuh (FP32 / BF16 sweeps exist only in that form); otherwise M is
+// the matrix or ILU factors [n][ns] and the vectors are in natural order.
 bool sweep3_supported(const LevelView& L, int kind);
 cudaError_t launch_sweep3(const LevelView& L, int kind, int dir, const void* M, const float* sc1, const float* sc2,
                           const void* dinv, double w, const void* b, void* u, SweepWs* ws, int* err,

@@ -140,6 +140,13 @@ __device__ __forceinline__ Val rec_val(const uint4 (&q)[CH], int slot) {
   }
 }
 
+// A vector-type value (double or float) at byte offset OFF of a record.
+template <typename Vv, int CH>
+__device__ __forceinline__ Vv rec_vec(const uint4 (&q)[CH], int off) {
+  if constexpr (sizeof(Vv) == 8) return __hiloint2double((int)rec_word(q, off / 4 + 1), (int)rec_word(q, off / 4));
+  else return __uint_as_float(rec_word(q, off / 4));
+}
+
 template <int W>
 struct Shared3 {
   int wdone[W][kMaxWarpsPerPlane];  // per compute warp: all local steps < value are finished
@@ -162,8 +169,10 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
   using Val = typename Prec<PK>::val;
   using S = Shape<NS>;
   constexpr int SA = S::SA, SB = S::SB, EC = S::EC;
-  constexpr bool SPLIT = REC && (KIND == SW_ILU_L || KIND == SW_ILU_U);
-  using R = IluRec<PK, NS, KIND == SW_ILU_U>;
+  // REC: records and vectors in the skewed layout (ilurec.cuh); otherwise
+  // the matrix [n][NS] and vectors in natural order
+  constexpr bool SPLIT = REC;
+  using R = SweepRec<PK, NS, KIND == SW_ILU_L ? 0 : (KIND == SW_ILU_U ? 1 : 2)>;
   // FOLD (FP64 / FP32): the sum of a point starts from b and subtracts its
   // terms.  BF16 keeps b apart (the row scale multiplies the sum only).
   constexpr bool FOLD = PK != KBF;
@@ -180,6 +189,7 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
   // shared value ring: hist[plane][k % kRing][column]
   V* hist = (V*)dyn_smem;
   const int ngroups = (g.nx + W - 1) / W;
+  for (int t = threadIdx.x; t < W * kRing * NW * 32; t += blockDim.x) hist[t] = V(0);
 
   for (;;) {
     __syncthreads();
@@ -283,10 +293,34 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
         int have_left = (w == 0) ? kDone : INT_MIN;        // cached progress of the left warp
         int have_right = (w + 1 == NW) ? kDone : INT_MIN;  // cached progress of the right warp
         int have_up = INT_MIN;                             // cached progress of the previous plane
-        const long long colbase = ((long long)i * g.ny + j) * g.nz;
+        // vector index of (i + dx, j + dy, kk): natural order, or the skewed
+        // layout (row (kk + SB*(j + dy)) mod nz, from the lane's row base)
+        const int br0 = SPLIT ? (SB * j) % g.nz : 0;
+        auto vslot = [&](int dx, int dy, int kk) -> long long {
+          if constexpr (SPLIT) {
+            int r = br0 + SB * dy + kk;
+            r = r >= g.nz ? r - g.nz : r;
+            r = r >= g.nz ? r - g.nz : r;
+            r = r < 0 ? r + g.nz : r;
+            return ((long long)(i + dx) * g.nz + r) * g.ny + (j + dy);
+          } else {
+            return ((long long)(i + dx) * g.ny + (j + dy)) * g.nz + kk;
+          }
+        };
+        // first 16-byte unit of the record of this lane's point kk (skewed
+        // layout); chunk c is at unit + c * ny
+        auto rec_unit = [&](int kk) -> long long {
+          int r = br0 + kk;
+          r = r >= g.nz ? r - g.nz : r;
+          r = r >= g.nz ? r - g.nz : r;
+          return ((long long)i * g.nz + r) * R::CHUNKS * g.ny + j;
+        };
 
-        // stage 2: operands of point K+2, loaded at step s, pre-summed at s+1
+        // stage 2: operands of point K+2, loaded at step s, pre-summed at s+1.
+        // A split record stays as loaded (q2) and is unpacked where it is
+        // used, so no instruction waits on a load in the step that issues it.
         Val c2[NS];
+        uint4 q2[SPLIT ? R::CHUNKS : 1];
         V x2[NS];
         V b2 = V(0), d2 = V(0), uo2 = V(0);
         float s2 = 1.0f;
@@ -302,18 +336,32 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
           cfK[e] = cfN[e] = Val(0);
           x2[e] = x1[e] = V(0);
         }
+#pragma unroll
+        for (int c = 0; c < (SPLIT ? R::CHUNKS : 1); ++c) q2[c] = make_uint4(0u, 0u, 0u, 0u);
+        // coefficient e of the stage-2 point (unpacked at use)
+        auto coef2 = [&](int e) -> Val {
+          if constexpr (SPLIT) return rec_val<Val>(q2, R::slot(e));
+          else return c2[e];
+        };
 
-        // value of neighbour e of sweep point KK (grid index k of KK given)
+        // value of neighbour e of sweep point KK (grid index k of KK given).
+        // The load is issued unconditionally: a neighbour off the grid has a
+        // coefficient of exactly zero (zero padding), so it reads the point's
+        // own right-hand side instead (finite, in bounds) and the term adds
+        // zero -- no select has to wait for the load.
         auto nb = [&](int e, int kk) -> V {
           const int ox = S::o(e, 0), oy = S::o(e, 1), oz = S::o(e, 2);
           const bool in = (unsigned)(i + ox) < (unsigned)g.nx && (unsigned)(j + oy) < (unsigned)g.ny &&
                           (unsigned)(kk + oz) < (unsigned)g.nz;
-          if (!in) return V(0);
-          const V* q = u + colbase + kk + P.lin[e];
+          const V* q = in ? u + vslot(ox, oy, kk + oz) : b + vslot(0, 0, kk);
           // the previous schedule plane of another CTA: read through L2;
-          // everything else (this CTA's planes, old values) through L1
-          return ((DIR * ox < 0) && p == 0) ? __ldcg(q) : *q;
+          // everything else (this CTA's planes, old values) through L1 (the
+          // choice is uniform per warp, and known at compile time for W == 1)
+          return (DIR * ox < 0 && (W == 1 || p == 0)) ? __ldcg(q) : *q;
         };
+        // value of the left column's point kk from the shared ring; the ring
+        // starts zeroed, so a slot read off the grid (coefficient zero) is finite
+        auto ring = [&](int kk) -> V { return hp[(kk & (kRing - 1)) * (NW * 32) + (J > 0 ? J - 1 : 0)]; };
 
         bool aborted = false;
         for (int s = s_begin; s <= s_end; ++s) {
@@ -380,21 +428,25 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
               if (use<NS, KIND, DIR, X>(e) != U_PRE) continue;
               V tv;
               if (cls<NS, KIND, DIR>(e) == T_Y) {
-                const int kk = K + 1 + DIR * S::o(e, 2);  // sweep index of the left column's point
-                tv = (J > 0 && kk >= 0 && kk < g.nz) ? hp[(kk & (kRing - 1)) * (NW * 32) + J - 1] : V(0);
+                tv = ring(K + 1 + DIR * S::o(e, 2));  // sweep index of the left column's point
               } else {
                 tv = x2[e];
               }
-              a = fma(sg * (V)to_c(c2[e]), tv, a);
+              a = fma(sg * (V)to_c(coef2(e)), tv, a);
             }
             accN = a;
             bN = b2;
-            dN = d2;
-            sN = s2;
+            if constexpr (SPLIT && R::HAS_D) dN = rec_vec<V>(q2, R::D_OFF);
+            else dN = d2;
+            if constexpr (SPLIT && R::HAS_S) sN = __uint_as_float(rec_word(q2, R::S_OFF / 4));
+            else sN = s2;
             uoN = uo2;
           }
 #pragma unroll
-          for (int e = 0; e < NS; ++e) cfN[e] = c2[e];
+          for (int e = 0; e < NS; ++e) {
+            const int us = use<NS, KIND, DIR, X>(e);
+            if (us == U_FIN0 || us == U_FIN1 || us == U_FINR) cfN[e] = coef2(e);
+          }
 
           // (c) finish point K
           if (okK) {
@@ -407,8 +459,7 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
               if (cls<NS, KIND, DIR>(e) == T_OWN) {
                 tv = carry;
               } else if (cls<NS, KIND, DIR>(e) == T_Y) {
-                const int kk = K + DIR * S::o(e, 2);
-                tv = (J > 0 && kk >= 0 && kk < g.nz) ? hp[(kk & (kRing - 1)) * (NW * 32) + J - 1] : V(0);
+                tv = ring(K + DIR * S::o(e, 2));
               } else {
                 tv = us == U_FIN0 ? x0[e] : x1[e];
               }
@@ -422,7 +473,7 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
               r = (FOLD ? a : bK - a) * dK;
               if (KIND != SW_ILU_U && relax) r = (KIND == SW_GS_ZERO) ? wv * r : (V(1) - wv) * uoK + wv * r;
             }
-            u[colbase + kK] = r;
+            u[vslot(0, 0, kK)] = r;
             hp[(K & (kRing - 1)) * (NW * 32) + J] = r;
             carry = r;
           }
@@ -450,20 +501,16 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
           const int K2 = K + 2;
           if (colok && K2 >= 0 && K2 < g.nz) {
             const int k2 = DIR > 0 ? K2 : g.nz - 1 - K2;
-            const long long p2 = colbase + k2;
-            if (SPLIT) {
-              uint4 q[R::CHUNKS];
-              const uint4* rp = (const uint4*)((const char*)P.M + p2 * R::BYTES);
+            const long long p2 = vslot(0, 0, k2);
+            if constexpr (SPLIT) {
+              const uint4* rp = (const uint4*)P.M + rec_unit(k2);
 #pragma unroll
-              for (int c = 0; c < R::CHUNKS; ++c) q[c] = __ldg(rp + c);
+              for (int c = 0; c < R::CHUNKS; ++c) q2[c] = __ldg(rp + (long long)c * g.ny);
+              if (K2 + kPrefetch < g.nz) {
+                const uint4* pf = (const uint4*)P.M + rec_unit(k2 + DIR * kPrefetch);
 #pragma unroll
-              for (int e = 0; e < NS; ++e) {
-                if (use<NS, KIND, DIR, X>(e) == U_NONE) continue;
-                c2[e] = rec_val<Val>(q, KIND == SW_ILU_L ? e : e - EC - 1);
+                for (int c = 0; c < R::CHUNKS; ++c) prefetch_l2(pf + (long long)c * g.ny);
               }
-              if (R::HAS_D) d2 = (V)rec_val<Val>(q, R::D_OFF / (int)sizeof(Val));
-              if (R::HAS_S) s2 = __uint_as_float(rec_word(q, R::S_OFF / 4));
-              if (KIND == SW_ILU_U && !R::HAS_D) d2 = dinv[p2];
             } else {
               const Val* __restrict__ a = (const Val*)P.M + p2 * NS;
 #pragma unroll
@@ -471,18 +518,18 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
                 if (use<NS, KIND, DIR, X>(e) != U_NONE) c2[e] = a[e];
               if (NEED_D) d2 = dinv[p2];
               if (PK == KBF) s2 = P.scale[p2];
+              if (K2 + kPrefetch < g.nz) {
+                constexpr int RB = NS * (int)sizeof(Val);
+                const char* pf = (const char*)P.M + (p2 + DIR * kPrefetch) * RB;
+                prefetch_l2(pf);
+                prefetch_l2(pf + RB - 1);
+              }
             }
 #pragma unroll
             for (int e = 0; e < NS; ++e)
               if (use<NS, KIND, DIR, X>(e) == U_PRE && cls<NS, KIND, DIR>(e) != T_Y) x2[e] = nb(e, k2);
             b2 = b[p2];
             if (KIND == SW_GS_FULL && relax) uo2 = u[p2];
-            if (K2 + kPrefetch < g.nz) {
-              constexpr int RB = SPLIT ? R::BYTES : NS * (int)sizeof(Val);
-              const char* pf = (const char*)P.M + (p2 + DIR * kPrefetch) * RB;
-              prefetch_l2(pf);
-              prefetch_l2(pf + RB - 1);
-            }
           }
         }
         if (lane == 0) st_rel_cta(&sh.wdone[p][w], kDone);
@@ -535,19 +582,26 @@ cudaError_t launch_kind(int kind, int dir, bool rec, const Sweep3Params& P, cuda
     kern<<<grid, nthr, smem, st>>>(P);
     return cudaGetLastError();
   };
-  if (kind == SW_GS_ZERO) return go(k_sweep3<PK, NS, SW_GS_ZERO, 1, W, X, 0>);
-  if (kind == SW_GS_FULL) {
-    if (dir > 0) return go(k_sweep3<PK, NS, SW_GS_FULL, 1, W, X, 0>);
-    return go(k_sweep3<PK, NS, SW_GS_FULL, -1, W, X, 0>);
-  }
+  // rec: records and vectors in the skewed layout.  The natural layout (the
+  // matrix [n][NS], vectors in natural order) is kept for FP64 only, where
+  // the context-free entry point uses it.
   if constexpr (PK == K64) {
-    // the unsplit factors are read only by the context-free entry point (FP64)
     if (!rec) {
+      if (kind == SW_GS_ZERO) return go(k_sweep3<PK, NS, SW_GS_ZERO, 1, W, X, 0>);
+      if (kind == SW_GS_FULL) {
+        if (dir > 0) return go(k_sweep3<PK, NS, SW_GS_FULL, 1, W, X, 0>);
+        return go(k_sweep3<PK, NS, SW_GS_FULL, -1, W, X, 0>);
+      }
       if (kind == SW_ILU_L) return go(k_sweep3<PK, NS, SW_ILU_L, 1, W, X, 0>);
       return go(k_sweep3<PK, NS, SW_ILU_U, -1, W, X, 0>);
     }
   } else {
     if (!rec) return cudaErrorNotSupported;
+  }
+  if (kind == SW_GS_ZERO) return go(k_sweep3<PK, NS, SW_GS_ZERO, 1, W, X, 1>);
+  if (kind == SW_GS_FULL) {
+    if (dir > 0) return go(k_sweep3<PK, NS, SW_GS_FULL, 1, W, X, 1>);
+    return go(k_sweep3<PK, NS, SW_GS_FULL, -1, W, X, 1>);
   }
   if (kind == SW_ILU_L) return go(k_sweep3<PK, NS, SW_ILU_L, 1, W, X, 1>);
   return go(k_sweep3<PK, NS, SW_ILU_U, -1, W, X, 1>);

@@ -519,10 +519,12 @@ def test_launch_counter_counts_kernels(S):
     c0 = S.launch_count()
     h.vcycle(r, z)
     per = S.launch_count() - c0
-    # 3 levels above the coarsest would be: per level 2 pre + 2 post sweeps,
-    # residual, restriction, prolongation; plus the coarsest solve
+    # per level above the coarsest: pre-smoothing (right-hand side into the
+    # sweeps' skewed layout, 2 sweeps, result back), post-smoothing (right-hand
+    # side and iterate in, 2 sweeps, result back), residual, restriction,
+    # prolongation; plus the coarsest solve
     nl = h.nlevels
-    assert per == 7 * (nl - 1) + 1
+    assert per == 12 * (nl - 1) + 1
     hg = make(S, d, off, A, use_graph=1)
     c0 = S.launch_count()
     hg.vcycle(r, z)
