@@ -238,6 +238,24 @@ class MG:
             lib().orc_mg_level_array(self.h, l, which, _p(out))
         return out
 
+    def level_apply32(self, l, op, x=None, b=None, y=None):
+        """One FP32 / BF16 level operation of a reduced-precision hierarchy
+        (orc_mg_level_apply32): op 0 y = b - A x, 1 / 2 forward / backward
+        Gauss-Seidel sweep on x (in place, returned), 3 y = ILU(0) apply of b,
+        4 y = R x, 5 y += P x.  Vectors are float32; returns the output."""
+        f32 = lambda a: None if a is None else np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+        x, b, y = f32(x), f32(b), f32(y)
+        if op in (1, 2):
+            x = x.copy()
+        elif op == 5:
+            y = y.copy()
+        nul = ctypes.c_void_p()
+        rc = lib().orc_mg_level_apply32(self.h, l, op, nul if x is None else _p(x), nul if b is None else _p(b),
+                                        nul if y is None else _p(y))
+        if rc:
+            raise ValueError("level_apply32: operation %d unavailable on level %d" % (op, l))
+        return x if op in (1, 2) else y
+
     def vcycle(self, r):
         r = _f64(r)
         z = np.zeros_like(r)

@@ -750,9 +750,9 @@ void orc_mg_free(void* h) {
 
 /* Build the hierarchy: Galerkin coarse operators by orc_rap27 (kept on the
  * offsets a chain reaches, in lexicographic order), smoother set-up on every
- * non-coarsest level, dense LU of the coarsest.  precision: 0 FP64, 1 FP32,
- * 2 BF16 with row scales; the reduced-precision cycles exist for scalar
- * problems only (B == 1), other combinations are rejected. */
+ * non-coarsest level, dense LU of the coarsest.  precision: 0 FP64, 1 FP32
+ * (scalar or 3x3 blocks), 2 BF16 with row scales (scalar only); other
+ * combinations are rejected. */
 int orc_mg_setup(void** out, const int d[3], int ns, const int* off, int B, const double* A, int smoother,
                  int transfer, double w, int precision, int max_levels) {
   *out = NULL;
@@ -762,7 +762,7 @@ int orc_mg_setup(void** out, const int d[3], int ns, const int* off, int B, cons
   if (B == 3 && smoother != SM_SGS) return ORC_EINVAL;
   if (smoother < SM_SGS || smoother > SM_LGS) return ORC_EINVAL;
   if (smoother == SM_LGS && (precision != 0 || w != 1.0)) return ORC_EINVAL;
-  if (precision != 0 && B != 1) return ORC_EINVAL;
+  if (precision == 2 && B != 1) return ORC_EINVAL; /* BF16 row scales: scalar problems only */
   for (int t = 0; t < 3; ++t)
     if (d[t] < 1) return ORC_EINVAL;
   orc_mg* mg = (orc_mg*)calloc(1, sizeof(orc_mg));
@@ -819,7 +819,16 @@ int orc_mg_setup(void** out, const int d[3], int ns, const int* off, int B, cons
         }
       }
       if (rc) break;
-      if (precision) {
+      if (precision && B == 3) {
+        /* FP32 blocks: every coefficient and the FP64 block inverse cast */
+        long nb2 = n * L->ns * 9;
+        L->Av = (float*)malloc(sizeof(float) * nb2);
+        L->As = (float*)malloc(sizeof(float) * n);
+        L->Dv32 = (float*)malloc(sizeof(float) * n * 9);
+        for (long t = 0; t < nb2; ++t) L->Av[t] = (float)L->A[t];
+        for (long p = 0; p < n; ++p) L->As[p] = 1.0f;
+        for (long t = 0; t < n * 9; ++t) L->Dv32[t] = (float)L->Dinv[t];
+      } else if (precision) {
         int mode = precision == 2 ? 2 : 1;
         L->Av = (float*)malloc(sizeof(float) * n * L->ns);
         L->As = (float*)malloc(sizeof(float) * n);
@@ -873,13 +882,13 @@ long orc_mg_level_array(void* h, int l, int which, void* dst) {
     case 0: src = L->A; cnt = n * L->ns * B2; break;
     case 1: src = L->LU; cnt = L->LU ? n * L->ns : 0; break;
     case 2: src = L->Dinv ? (const void*)L->Dinv : (const void*)L->Udinv; cnt = L->Dinv ? n * B2 : (L->Udinv ? n : 0); break;
-    case 3: src = L->Av; cnt = L->Av ? n * L->ns : 0; sz = 4; break;
+    case 3: src = L->Av; cnt = L->Av ? n * L->ns * B2 : 0; sz = 4; break;
     case 4: src = L->As; cnt = L->As ? n : 0; sz = 4; break;
     case 5: src = L->Lv; cnt = L->Lv ? n * L->ns : 0; sz = 4; break;
     case 6: src = L->Ls; cnt = L->Ls ? n : 0; sz = 4; break;
     case 7: src = L->Uv; cnt = L->Uv ? n * L->ns : 0; sz = 4; break;
     case 8: src = L->Us; cnt = L->Us ? n : 0; sz = 4; break;
-    case 9: src = L->Dv32; cnt = L->Dv32 ? n : 0; sz = 4; break;
+    case 9: src = L->Dv32; cnt = L->Dv32 ? n * B2 : 0; sz = 4; break;
   }
   if (src && dst && cnt) memcpy(dst, src, cnt * sz);
   return src ? cnt : 0;
@@ -954,39 +963,73 @@ static void vcycle64(orc_mg* mg, const double* r, double* z) {
 }
 
 /* ---- reduced-precision V-cycle: all level arithmetic in FP32 ------------- */
+/* The paper has no reduced-precision cycle; this is the build's extension.
+ * Scalar levels keep FP32 values, or BF16 values with an FP32 row scale s_p;
+ * 3x3-block levels keep FP32 blocks and the FP32 cast of the FP64 block
+ * inverse.  Every sum is accumulated in FP32, in the loop order below. */
 
-/* r = b - s_p * sum_e v_pe x_q   (FP32; s_p == 1 in FP32 mode) */
-static void residual32(const orc_level* L, const float* b, const float* x, float* r) {
+/* t_r = s_p * sum_e sum_c v_{p,e,r,c} x_{p+e,c}: the stencil row sum of point
+ * (i,j,k) in FP32, the row scale applied to the finished sum (scalar levels;
+ * it is 1 in FP32 mode), the centre left out when skip_centre. */
+static void rowsum32(const orc_level* L, int B, const float* x, int i, int j, int k, int skip_centre, float* t) {
   const int* d = L->d;
+  long p = pidx(d, i, j, k);
+  for (int r = 0; r < B; ++r) {
+    float s = 0.0f;
+    for (int e = 0; e < L->ns; ++e) {
+      const int* o = L->off + 3 * e;
+      if (skip_centre && (o[0] | o[1] | o[2]) == 0) continue;
+      if (!inside(d, i + o[0], j + o[1], k + o[2])) continue;
+      long q = pidx(d, i + o[0], j + o[1], k + o[2]);
+      for (int c = 0; c < B; ++c) s += L->Av[((p * L->ns + e) * B + r) * B + c] * x[q * B + c];
+    }
+    t[r] = B == 1 ? L->As[p] * s : s;
+  }
+}
+
+/* r = b - A x in FP32 */
+static void residual32(const orc_level* L, int B, const float* b, const float* x, float* r) {
+  const int* d = L->d;
+  float t[3];
   for (int i = 0; i < d[0]; ++i)
     for (int j = 0; j < d[1]; ++j)
       for (int k = 0; k < d[2]; ++k) {
         long p = pidx(d, i, j, k);
-        float s = 0.0f;
-        for (int e = 0; e < L->ns; ++e) {
-          const int* o = L->off + 3 * e;
-          if (!inside(d, i + o[0], j + o[1], k + o[2])) continue;
-          s += L->Av[p * L->ns + e] * x[pidx(d, i + o[0], j + o[1], k + o[2])];
-        }
-        r[p] = b[p] - L->As[p] * s;
+        rowsum32(L, B, x, i, j, k, 0, t);
+        for (int c = 0; c < B; ++c) r[p * B + c] = b[p * B + c] - t[c];
       }
 }
 
-/* Gauss-Seidel in FP32: u_p = (b_p - s_p * sum_{o!=0} v_po u_q) * dinv_p.
- * dir +1 lexicographic, -1 reverse. */
-static void gs32(const orc_level* L, const float* b, float* u, int dir) {
+/* One point of Gauss-Seidel in FP32: g = b_p - sum_{o != 0} A_po u_{p+o}, then
+ * u_p = dinv_p g (scalar) or u_p = Dinv_p g (3x3 block, row by row). */
+static void gs32_point(const orc_level* L, int B, const float* b, float* u, int i, int j, int k) {
   const int* d = L->d;
-  long n = npts(d);
-  for (long t = 0; t < n; ++t) {
-    long p = dir > 0 ? t : n - 1 - t;
-    int k = (int)(p % d[2]), j = (int)((p / d[2]) % d[1]), i = (int)(p / ((long)d[1] * d[2]));
-    float s = 0.0f;
-    for (int e = 0; e < L->ns; ++e) {
-      const int* o = L->off + 3 * e;
-      if ((o[0] | o[1] | o[2]) == 0 || !inside(d, i + o[0], j + o[1], k + o[2])) continue;
-      s += L->Av[p * L->ns + e] * u[pidx(d, i + o[0], j + o[1], k + o[2])];
-    }
-    u[p] = (b[p] - L->As[p] * s) * L->Dv32[p];
+  long p = pidx(d, i, j, k);
+  float t[3], g[3];
+  rowsum32(L, B, u, i, j, k, 1, t);
+  for (int c = 0; c < B; ++c) g[c] = b[p * B + c] - t[c];
+  if (B == 1) {
+    u[p] = g[0] * L->Dv32[p];
+    return;
+  }
+  for (int r = 0; r < B; ++r) {
+    float v = 0.0f;
+    for (int c = 0; c < B; ++c) v += L->Dv32[(p * B + r) * B + c] * g[c];
+    u[p * B + r] = v;
+  }
+}
+
+/* Gauss-Seidel sweep in FP32, dir +1 lexicographic, -1 reverse. */
+static void gs32(const orc_level* L, int B, const float* b, float* u, int dir) {
+  const int* d = L->d;
+  if (dir > 0) {
+    for (int i = 0; i < d[0]; ++i)
+      for (int j = 0; j < d[1]; ++j)
+        for (int k = 0; k < d[2]; ++k) gs32_point(L, B, b, u, i, j, k);
+  } else {
+    for (int i = d[0] - 1; i >= 0; --i)
+      for (int j = d[1] - 1; j >= 0; --j)
+        for (int k = d[2] - 1; k >= 0; --k) gs32_point(L, B, b, u, i, j, k);
   }
 }
 
@@ -1018,7 +1061,8 @@ static void ilu32(const orc_level* L, const float* r, float* x) {
   }
 }
 
-static void restrict32(int transfer, const int fd[3], const float* rf, float* fc) {
+/* fc = R rf in FP32 (weights exact in FP32), per unknown, support order. */
+static void restrict32(int transfer, const int fd[3], int B, const float* rf, float* fc) {
   int cd[3];
   orc_coarse_dims_t(transfer, fd, cd);
   for (int I0 = 0; I0 < cd[0]; ++I0)
@@ -1026,67 +1070,72 @@ static void restrict32(int transfer, const int fd[3], const float* rf, float* fc
       for (int I2 = 0; I2 < cd[2]; ++I2) {
         int I[3] = {I0, I1, I2}, base[3], span[3];
         support(transfer, I, base, span);
-        float s = 0.0f;
-        for (int a = 0; a < span[0]; ++a)
-          for (int b = 0; b < span[1]; ++b)
-            for (int c = 0; c < span[2]; ++c) {
-              int u[3] = {base[0] + a, base[1] + b, base[2] + c};
-              if (!inside(fd, u[0], u[1], u[2])) continue;
-              s += (float)rweight(transfer, I, u) * rf[pidx(fd, u[0], u[1], u[2])];
-            }
-        fc[pidx(cd, I0, I1, I2)] = s;
+        for (int r = 0; r < B; ++r) {
+          float s = 0.0f;
+          for (int a = 0; a < span[0]; ++a)
+            for (int b = 0; b < span[1]; ++b)
+              for (int c = 0; c < span[2]; ++c) {
+                int u[3] = {base[0] + a, base[1] + b, base[2] + c};
+                if (!inside(fd, u[0], u[1], u[2])) continue;
+                s += (float)rweight(transfer, I, u) * rf[pidx(fd, u[0], u[1], u[2]) * B + r];
+              }
+          fc[pidx(cd, I0, I1, I2) * B + r] = s;
+        }
       }
 }
 
-static void prolong32(int transfer, const int fd[3], const float* ec, float* uf) {
+/* uf += P ec in FP32: the interpolated value is summed first, then added. */
+static void prolong32(int transfer, const int fd[3], int B, const float* ec, float* uf) {
   int cd[3];
   orc_coarse_dims_t(transfer, fd, cd);
   for (int v0 = 0; v0 < fd[0]; ++v0)
     for (int v1 = 0; v1 < fd[1]; ++v1)
       for (int v2 = 0; v2 < fd[2]; ++v2) {
         int v[3] = {v0, v1, v2};
-        float s = 0.0f;
-        for (int a = -1; a <= 1; ++a)
-          for (int b = -1; b <= 1; ++b)
-            for (int c = -1; c <= 1; ++c) {
-              int J[3] = {coarse_of(transfer, 0, v0) + a, coarse_of(transfer, 1, v1) + b,
-                          coarse_of(transfer, 2, v2) + c};
-              if (!inside(cd, J[0], J[1], J[2])) continue;
-              double wgt = pweight(transfer, v, J);
-              if (wgt == 0.0) continue;
-              s += (float)wgt * ec[pidx(cd, J[0], J[1], J[2])];
-            }
-        uf[pidx(fd, v0, v1, v2)] += s;
+        for (int r = 0; r < B; ++r) {
+          float s = 0.0f;
+          for (int a = -1; a <= 1; ++a)
+            for (int b = -1; b <= 1; ++b)
+              for (int c = -1; c <= 1; ++c) {
+                int J[3] = {coarse_of(transfer, 0, v0) + a, coarse_of(transfer, 1, v1) + b,
+                            coarse_of(transfer, 2, v2) + c};
+                if (!inside(cd, J[0], J[1], J[2])) continue;
+                double wgt = pweight(transfer, v, J);
+                if (wgt == 0.0) continue;
+                s += (float)wgt * ec[pidx(cd, J[0], J[1], J[2]) * B + r];
+              }
+          uf[pidx(fd, v0, v1, v2) * B + r] += s;
+        }
       }
 }
 
 static void vcycle32(orc_mg* mg, const double* r, double* z) {
-  int Lc = mg->nlev;
+  int Lc = mg->nlev, B = mg->B;
   float *f[16], *u[16];
   for (int l = 0; l < Lc; ++l) {
-    long n = npts(mg->lev[l].d);
+    long n = npts(mg->lev[l].d) * B;
     f[l] = (float*)malloc(sizeof(float) * n);
     u[l] = (float*)malloc(sizeof(float) * n);
   }
-  long n0 = npts(mg->lev[0].d);
+  long n0 = npts(mg->lev[0].d) * B;
   for (long t = 0; t < n0; ++t) f[0][t] = (float)r[t];
   for (int l = 0; l < Lc - 1; ++l) {
     orc_level* L = &mg->lev[l];
-    long n = npts(L->d);
+    long n = npts(L->d) * B;
     float* res = (float*)malloc(sizeof(float) * n);
     if (mg->smoother == SM_SGS) {
       for (long t = 0; t < n; ++t) u[l][t] = 0.0f;
-      gs32(L, f[l], u[l], +1);
-      gs32(L, f[l], u[l], -1);
+      gs32(L, B, f[l], u[l], +1);
+      gs32(L, B, f[l], u[l], -1);
     } else {
       ilu32(L, f[l], u[l]);
     }
-    residual32(L, f[l], u[l], res);
-    restrict32(mg->transfer, L->d, res, f[l + 1]);
+    residual32(L, B, f[l], u[l], res);
+    restrict32(mg->transfer, L->d, B, res, f[l + 1]);
     free(res);
   }
   {
-    long n = npts(mg->lev[Lc - 1].d);
+    long n = npts(mg->lev[Lc - 1].d) * B;
     double *fd = (double*)malloc(sizeof(double) * n), *ud = (double*)malloc(sizeof(double) * n);
     for (long t = 0; t < n; ++t) fd[t] = (double)f[Lc - 1][t];
     coarse_solve64(mg, fd, ud);
@@ -1095,14 +1144,14 @@ static void vcycle32(orc_mg* mg, const double* r, double* z) {
   }
   for (int l = Lc - 2; l >= 0; --l) {
     orc_level* L = &mg->lev[l];
-    long n = npts(L->d);
-    prolong32(mg->transfer, L->d, u[l + 1], u[l]);
+    long n = npts(L->d) * B;
+    prolong32(mg->transfer, L->d, B, u[l + 1], u[l]);
     if (mg->smoother == SM_SGS) {
-      gs32(L, f[l], u[l], +1);
-      gs32(L, f[l], u[l], -1);
+      gs32(L, B, f[l], u[l], +1);
+      gs32(L, B, f[l], u[l], -1);
     } else {
       float *res = (float*)malloc(sizeof(float) * n), *x = (float*)malloc(sizeof(float) * n);
-      residual32(L, f[l], u[l], res);
+      residual32(L, B, f[l], u[l], res);
       ilu32(L, res, x);
       for (long t = 0; t < n; ++t) u[l][t] += x[t];
       free(res); free(x);
@@ -1110,6 +1159,30 @@ static void vcycle32(orc_mg* mg, const double* r, double* z) {
   }
   for (long t = 0; t < n0; ++t) z[t] = (double)u[0][t];
   for (int l = 0; l < Lc; ++l) { free(f[l]); free(u[l]); }
+}
+
+/* One reduced-precision level operation of a hierarchy set up with precision
+ * 1 or 2 (for the pins of the FP32 / BF16 arithmetic), on FP32 vectors of
+ * level l: op 0 y = b - A x; 1 x <- GS forward sweep; 2 x <- GS backward
+ * sweep; 3 y = U^-1 L^-1 b (ILU(0) apply); 4 y = R x (x on level l, y on
+ * l+1); 5 y += P x (x on level l+1, y on level l).  Returns ORC_EINVAL when
+ * the operation does not exist for this hierarchy. */
+int orc_mg_level_apply32(void* h, int l, int op, float* x, const float* b, float* y) {
+  orc_mg* mg = (orc_mg*)h;
+  if (!mg->precision || l < 0 || l >= mg->nlev) return ORC_EINVAL;
+  orc_level* L = &mg->lev[l];
+  const int last = l == mg->nlev - 1;
+  switch (op) {
+    case 0: if (!L->Av) return ORC_EINVAL; residual32(L, mg->B, b, x, y); return ORC_OK;
+    case 1: case 2:
+      if (mg->smoother != SM_SGS || !L->Av) return ORC_EINVAL;
+      gs32(L, mg->B, b, x, op == 1 ? +1 : -1);
+      return ORC_OK;
+    case 3: if (mg->smoother != SM_ILU0 || !L->Lv) return ORC_EINVAL; ilu32(L, b, y); return ORC_OK;
+    case 4: if (last) return ORC_EINVAL; restrict32(mg->transfer, L->d, mg->B, x, y); return ORC_OK;
+    case 5: if (last) return ORC_EINVAL; prolong32(mg->transfer, L->d, mg->B, x, y); return ORC_OK;
+  }
+  return ORC_EINVAL;
 }
 
 void orc_mg_vcycle(void* h, const double* r, double* z) {

@@ -339,25 +339,29 @@ def test_fgmres_block_solve_matches_oracle(S, orc):
     assert res < 1e-8
 
 
-def test_fp32_block_hierarchy_vcycle_and_fgmres(S, orc):
-    """The 3-unknown system with an FP32 hierarchy (block GS in float).  The
-    oracle has no reduced-precision block cycle, so the V-cycle is held to the
-    FP64 oracle's within FP32 accuracy (unit roundoff 6e-8 grown over the
-    cycle's sweeps and transfers: 1e-4), and the FGMRES solve must reach the
-    tolerance with the true residual recomputed by the oracle."""
-    d = (16, 16, 8)
+@pytest.mark.parametrize("d", [(16, 16, 8), (32, 24, 16)])
+def test_fp32_block_hierarchy_vcycle_and_fgmres(S, orc, d):
+    """The 3-unknown system with an FP32 hierarchy (block GS in float) against
+    the oracle's FP32 block cycle (same precision, own summation order:
+    TOL_LOWP), its FP64 cycle within FP32 accuracy, and an FGMRES solve that
+    reaches the tolerance with the true residual recomputed by the oracle in
+    the FP32 oracle's iteration count within one."""
     A = I.block7_layered(d, 7).numpy()
     r = I.rhs(np.prod(d) * 3, 12).numpy()
     h = make(S, d, I.OFF7, A, block=3, transfer=S.PC8C, precision=S.FP32, krylov=S.FGMRES, restart=30)
     z = torch.empty_like(cu(r))
     h.vcycle(cu(r), z)
-    ref = orc.MG(d, I.OFF7, A, B=3, transfer=orc.PC8C)
-    assert rel2(host(z), ref.vcycle(r)) < 1e-4
+    ref32 = orc.MG(d, I.OFF7, A, B=3, transfer=orc.PC8C, precision=orc.FP32)
+    assert rel2(host(z), ref32.vcycle(r)) < TOL_LOWP
+    ref64 = orc.MG(d, I.OFF7, A, B=3, transfer=orc.PC8C)
+    assert rel2(host(z), ref64.vcycle(r)) < 1e-4
     x = torch.zeros_like(cu(r))
     it, rr, rc = h.solve(cu(r), x, tol=1e-8, maxit=300)
     assert rc == 0 and rr < 1e-8
     res = np.linalg.norm(orc.residual(d, I.OFF7, A, r, host(x), B=3)) / np.linalg.norm(r)
     assert res < 1e-8
+    _, rcr, itr, _, _ = ref32.fgmres(r, tol=1e-8, restart=30, maxit=300)
+    assert rcr == 0 and abs(it - itr) <= 1
 
 
 def test_solves_are_deterministic(S):
