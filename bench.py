@@ -419,6 +419,7 @@ def oracle_sample(w, seed=0):
     import numpy as np
     from oracle import oracle as orc
     orc.build()
+    orc.set_threads(1)  # the oracle as written: one thread
     d = w["dims"]
     full = d[0] * d[1] * d[2]
     shrink = 1

@@ -545,15 +545,36 @@ int orc_rap27(int transfer, const int fd[3], int ns, const int* off, int B, cons
   long nc = npts(cd);
   memset(Ac27, 0, sizeof(double) * nc * 27 * B * B);
   for (int o = 0; o < 27; ++o) present[o] = 0;
-  for (int I0 = 0; I0 < cd[0]; ++I0)
-    for (int I1 = 0; I1 < cd[1]; ++I1)
-      for (int I2 = 0; I2 < cd[2]; ++I2) {
-        int I[3] = {I0, I1, I2};
-        long Pc = pidx(cd, I0, I1, I2);
-        int rc = rap_point(transfer, fd, cd, ns, off, B, Af, I, Ac27 + Pc * 27 * B * B, present);
-        if (rc) return rc;
+  int bad = 0;
+  /* Coarse points are independent (each sums its own chains into its own
+   * row), so they may run on several threads without changing any sum. */
+#pragma omp parallel
+  {
+    int pres[27] = {0};
+#pragma omp for schedule(dynamic, 64)
+    for (long Pc = 0; Pc < nc; ++Pc) {
+      int I[3] = {(int)(Pc / ((long)cd[1] * cd[2])), (int)((Pc / cd[2]) % cd[1]), (int)(Pc % cd[2])};
+      if (rap_point(transfer, fd, cd, ns, off, B, Af, I, Ac27 + Pc * 27 * B * B, pres)) {
+#pragma omp atomic write
+        bad = 1;
       }
-  return ORC_OK;
+    }
+#pragma omp critical
+    for (int o = 0; o < 27; ++o) present[o] |= pres[o];
+  }
+  return bad ? ORC_EINVAL : ORC_OK;
+}
+
+/* Threads of the parallel loops above (no effect in a serial build). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
 }
 
 /* The same chain sums for a list of coarse point indices only (for checking
