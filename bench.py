@@ -6,10 +6,13 @@ Galerkin products, smoother set-up, coarsest inverse) followed by the
 V-cycle-preconditioned Krylov solve to a relative residual of 1e-9 and the
 FP64 true-residual check, with the matrix and right-hand side already in HBM
 (the e2e figure adds the host<->device copies).  The metric is time to
-solution (lower is better); the V-cycle's HBM throughput and the dominant
-kernel's roofline fraction are reported beside it.
+solution (lower is better), reported for the FP64 hierarchy (`value`) and
+for the FP32 and row-scaled BF16 hierarchies under an FP64 outer iteration
+(`forms`, each with its error against the FP64 solution); the V-cycle's
+HBM throughput, its per-level cost and the dominant kernel's roofline
+fraction are reported beside it.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3]
   python bench.py --impl reference     (CPU oracle on a bounded sample)
 Multi-GPU runs are independent replicas (one problem per GPU, no collective
 on the data path); the reported time is the maximum over ranks.
@@ -36,6 +39,10 @@ WORKLOADS = {
     # the same problem at 128^3: the small case for detailed profiles (matrix 453 MB > L2)
     "c2_128": dict(desc="aniso27_128^3_ilu0_fw27v_pcg_fp64", dims=(128, 128, 128), gen="q1", smoother=1,
                    transfer=0, precision=0, krylov=0, tol=1e-9),
+    # the largest configuration that fits one GPU (56.6 M unknowns), three ways:
+    # FP64 hierarchy under PCG (value), FP32 and BF16 hierarchies under FPCG
+    "c3": dict(desc="aniso27_384^3_ilu0_fw27v_pcg", dims=(384, 384, 384), gen="q1", smoother=1, transfer=0,
+               precision=0, krylov=0, tol=1e-9, forms=(0, 1, 2)),
     "c3_fp64": dict(desc="aniso27_384^3_ilu0_pcg_fp64", dims=(384, 384, 384), gen="q1", smoother=1, transfer=0,
                     precision=0, krylov=0, tol=1e-9),
     "c3_fp32": dict(desc="aniso27_384^3_ilu0_fpcg_fp32hier", dims=(384, 384, 384), gen="q1", smoother=1,
@@ -79,9 +86,19 @@ WORKLOADS = {
     "c8": dict(desc="zaniso27_256^3_lgs_semicoarse_xy_fgmres30_fp64", dims=(256, 256, 256), gen="q1z", smoother=2,
                transfer=3, precision=0, krylov=2, tol=1e-9),
 }
-DEFAULT = "c2"
+DEFAULT = "c3"
 HBM_PEAK_FALLBACK = 6800.0
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 tensor path)
+FP64_PEAK_NOMINAL = 1.25  # TFLOP/s, used only when the measured figure is missing
+FP64_PROBE = os.path.join(ROOT, "profiles", "fp64_fma_peak_gb300.txt")
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel from one ncu capture of the current kernel on the same
+# problem family at a smaller size, scaled by the points of a full launch;
+# None where no capture of the current kernel exists
+TRAFFIC = {}
+
+
+PREC = {0: "fp64", 1: "fp32", 2: "bf16"}
+KRYLOV = {0: "PCG", 1: "FPCG", 2: "FGMRES(30)"}
 
 
 def log(*a):
@@ -138,6 +155,17 @@ def train_post_smoother(w, dev):
     return theta, {"train_s": round(train_s, 3), "pairs": steps * cfg["batch"], "fields": cfg["fields"],
                    "grid": list(cfg["dims"]), "loss_before": round(loss0, 6), "loss_after": round(loss1, 6),
                    "loss_last_steps": round(sum(losses[-20:]) / min(20, len(losses)), 6)}
+
+
+def fp64_peak():
+    """Measured FP64 FMA throughput (TFLOP/s) from the committed probe summary."""
+    try:
+        for line in open(FP64_PROBE):
+            if line.startswith("fp64_tflops:"):
+                return float(line.split(":")[1]), "measured FP64 FMA rate of this GPU (independent-FMA probe, CUDA events)"
+    except (OSError, ValueError):
+        pass
+    return FP64_PEAK_NOMINAL, "nominal GB300 FP64 rate (no measurement found)"
 
 
 def measured_peaks():
@@ -218,32 +246,41 @@ def run_ours(args, w, rank, world):
     B = w.get("block", 1)
     off, A, b, logk = make_problem(w, rank, dev, with_logk=True)
     n = b.numel()
-    x = torch.zeros_like(b)
     st = torch.cuda.current_stream()
-    kw = dict(block=B, smoother=w["smoother"], transfer=w["transfer"], precision=w["precision"],
-              krylov=w["krylov"], restart=30)
+    forms = list(w.get("forms", (w["precision"],)))
+    main_prec = forms[0]
+
+    def opts(prec):
+        # a reduced-precision hierarchy is only approximately symmetric: PCG
+        # becomes flexible PCG (FGMRES stays)
+        kry = w["krylov"] if (prec == 0 or w["krylov"] == 2) else 1
+        return dict(block=B, smoother=w["smoother"], transfer=w["transfer"], precision=prec, krylov=kry, restart=30)
+
     theta, learned_info = (None, None)
     if w.get("learned"):
         theta, learned_info = train_post_smoother(w, dev)
 
-    def make_ctx(Amat, lk=logk):
-        h = smg.SMG(w["dims"], off, Amat, **kw)
-        if theta is not None:
+    def make_ctx(prec, Amat, lk=logk):
+        h = smg.SMG(w["dims"], off, Amat, **opts(prec))
+        if theta is not None and prec == main_prec:
             h.set_learned_smoother(theta, lk)
         return h
 
-    def step():
-        h = make_ctx(A)
+    x = torch.zeros_like(b)
+
+    def step(prec):
+        h = make_ctx(prec, A)
         x.zero_()
         it, rr, rc = h.solve(b, x, tol=w["tol"], maxit=1000, check=False)
         s = h.stats()
         h.close()
-        return it, rr, rc, s
+        if rc != 0:
+            raise RuntimeError("solve failed (%s hierarchy): status %d (%s)" % (PREC[prec], rc, smg.strerror(rc)))
+        return it, rr, s
 
+    # ---- the main form: W warm-up steps, K timed steps --------------------
     for _ in range(args.warmup):
-        it, rr, rc, s = step()
-    if rc != 0:
-        raise RuntimeError("solve failed: status %d (%s)" % (rc, smg.strerror(rc)))
+        step(main_prec)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -253,127 +290,148 @@ def run_ours(args, w, rank, world):
     with Clocks(dev.index) as clk:
         ev0.record(st)
         for _ in range(args.steps):
-            results.append(step())
+            results.append(step(main_prec))
         ev1.record(st)
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     launches = smg.launch_count() - l0
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev, world)
-    iters = [r[0] for r in results]
-    relres = max(r[1] for r in results)
-    s = results[-1][3]
     clocks = clk.summary()
+    x_main = x.clone()
+    form_info = {PREC[main_prec]: {"krylov": KRYLOV[opts(main_prec)["krylov"]],
+                                   "time_to_solution_s": round(ms / 1e3, 5), "iterations": results[-1][0],
+                                   "final_true_relres": max(r[1] for r in results),
+                                   "setup_ms": round(results[-1][2]["setup_ms"], 3), "timed_steps": args.steps}}
 
-    # --- the same problem with the plain V-cycle and PCG, for comparison ------
+    # ---- the other forms: 1 warm-up, a few timed steps, error vs the main form
+    for prec in forms[1:]:
+        step(prec)
+        k = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        res = [step(prec) for _ in range(k)]
+        e1.record(st)
+        torch.cuda.synchronize()
+        err = float(torch.linalg.vector_norm(x - x_main) / torch.linalg.vector_norm(x_main))
+        form_info[PREC[prec]] = {"krylov": KRYLOV[opts(prec)["krylov"]],
+                                 "time_to_solution_s": round(e0.elapsed_time(e1) / k / 1e3, 5),
+                                 "iterations": res[-1][0], "final_true_relres": max(r[1] for r in res),
+                                 "setup_ms": round(res[-1][2]["setup_ms"], 3), "timed_steps": k,
+                                 "rel_error_vs_fp64_solution": err}
+    if len(forms) > 1:
+        for v in form_info.values():
+            v.setdefault("rel_error_vs_fp64_solution", 0.0)
+        form_info["error_reference"] = ("the GPU FP64-hierarchy solution of the same problem (its V-cycle and "
+                                        "iteration count are parity-checked against the oracle at 128^3 and 256^3)")
+
+    # ---- the same problem with the plain V-cycle and PCG (learned workload) ---
     plain = None
     if theta is not None:
-        hp = smg.SMG(w["dims"], off, A, **dict(kw, krylov=0))
+        hp = smg.SMG(w["dims"], off, A, **dict(opts(main_prec), krylov=0))
         hp.close()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        hp = smg.SMG(w["dims"], off, A, **dict(kw, krylov=0))
+        hp = smg.SMG(w["dims"], off, A, **dict(opts(main_prec), krylov=0))
         x.zero_()
         pit, prr, prc = hp.solve(b, x, tol=w["tol"], maxit=1000, check=False)
         hp.close()
         e1.record(st)
         torch.cuda.synchronize()
-        plain = {"krylov": "PCG", "smoother": "plain GS V-cycle", "ms": round(e0.elapsed_time(e1), 3),
-                 "iterations": pit, "final_true_relres": prr, "status": prc}
+        if prc != 0:
+            raise RuntimeError("plain PCG solve failed: status %d" % prc)
+        plain = {"krylov": "PCG", "smoother": "plain V-cycle", "ms": round(e0.elapsed_time(e1), 3),
+                 "iterations": pit, "final_true_relres": prr}
 
-    # --- V-cycle throughput on a persistent hierarchy (plain V-cycle) ----------
-    h = smg.SMG(w["dims"], off, A, **kw)
+    # ---- V-cycle throughput and per-level cost on a persistent hierarchy ----
     z = torch.empty_like(b)
-    for _ in range(2):
-        h.vcycle(b, z)
-    torch.cuda.synchronize()
-    nv = 5
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(nv):
-        h.vcycle(b, z)
-    e1.record(st)
-    torch.cuda.synchronize()
-    vc_ms = e0.elapsed_time(e1) / nv
-    vc_gbs = s["vcycle_bytes"] / (vc_ms * 1e-3) / 1e9
+    vcycles = {}
+    main_profile = None
+    for prec in forms:
+        h = smg.SMG(w["dims"], off, A, **opts(prec))
+        s = h.stats()
+        for _ in range(2):
+            h.vcycle(b, z)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nv = 5
+        e0.record(st)
+        for _ in range(nv):
+            h.vcycle(b, z)
+        e1.record(st)
+        torch.cuda.synchronize()
+        vc_ms = e0.elapsed_time(e1) / nv
+        profs = [h.vcycle_profile(b, z) for _ in range(3)]
+        h.close()
+        stage = {}
+        for prof in profs:
+            for lvl, name, t in prof:
+                stage.setdefault((lvl, name), []).append(t)
+        stage = {k: statistics.median(v) for k, v in stage.items()}
+        levels = {}
+        for (lvl, name), t in sorted(stage.items()):
+            e = levels.setdefault(lvl, {"dims": list(s["dims"][lvl]), "sweeps_ms": 0.0, "other_ms": 0.0})
+            e["sweeps_ms" if name in ("pre1", "pre2", "post1", "post2") else "other_ms"] += t
+        total = sum(e["sweeps_ms"] + e["other_ms"] for e in levels.values())
+        per_level = [{"level": lvl, "dims": e["dims"], "sweeps_ms": round(e["sweeps_ms"], 4),
+                      "other_ms": round(e["other_ms"], 4),
+                      "share": round((e["sweeps_ms"] + e["other_ms"]) / total, 4)} for lvl, e in sorted(levels.items())]
+        hbm = float(measured_peaks().get("hbm_gbs", HBM_PEAK_FALLBACK))
+        vcycles[PREC[prec]] = {"vcycle_ms": round(vc_ms, 4), "vcycle_bytes": s["vcycle_bytes"],
+                               "vcycle_gbs": round(s["vcycle_bytes"] / (vc_ms * 1e-3) / 1e9, 1),
+                               "vcycle_hbm_frac": round(s["vcycle_bytes"] / (vc_ms * 1e-3) / 1e9 / hbm, 4),
+                               "coarse_levels_share": round(1.0 - per_level[0]["share"], 4), "per_level": per_level}
+        if prec == main_prec:
+            main_profile = stage
+            stats_main = s
 
-    # --- dominant kernel: level-0 lower triangular sweep, timed live -----------
+    # ---- dominant kernel: the level-0 triangular (or line) sweep of a V-cycle --
     lvl0 = int(w["dims"][0]) * int(w["dims"][1]) * int(w["dims"][2])
     nsf = len(off)
     nlow = nsf // 2
-    cbytes = {0: 8, 1: 4, 2: 2}[w["precision"]]
-    vbytes = 8 if w["precision"] == 0 else 4
-    if w["precision"] == 0:
-        vec = torch.empty(lvl0 * B, dtype=torch.float64, device=dev)
-        rhs = b
-    else:
-        vec = torch.empty(lvl0 * B, dtype=torch.float32, device=dev)
-        rhs = b.float()
+    cbytes = {0: 8, 1: 4, 2: 2}[main_prec]
+    vbytes = 8 if main_prec == 0 else 4
+    sbytes = 4 if main_prec == 2 else 0
     ny = int(w["dims"][1])
-    kfile = ("k_sweep3" if ny <= 512 else "k_sweep2") if B == 1 else ("k_bsweep3" if ny <= 512 else "k_sweep (3x3 blocks)")
     if w["smoother"] == 2:
-        op, kname = smg.OP_LGS_FORWARD, "k_lsweep (line Gauss-Seidel forward, level 0)"
-        # column factors: 128 chunks of m rows, 5 doubles per chunk row after the
-        # first and 17 per chunk, per column of nz points
+        kname = "k_lsweep (line Gauss-Seidel, zero-guess forward, level 0)"
         nz = int(w["dims"][2])
         m = max(2, -(-nz // 128))
         fac_pt = 8.0 * ((m - 1) * 5 + 17) * 128 / nz
-        flops_pt, bytes_pt = 2 * (nsf - 3) + 10, nsf * cbytes + fac_pt + 3 * vbytes
-        vec.zero_()
-        run_k = lambda: h.level_apply(0, op, x=vec, b=rhs)
+        flops_pt, bytes_pt = 2 * (nlow - 1) + 10, nlow * cbytes + fac_pt + 2 * vbytes
     elif w["smoother"] == 1:
-        op, kname = smg.OP_ILU_LOWER, "%s (ILU(0) lower solve, level 0)" % kfile
-        flops_pt, bytes_pt = 2 * nlow + 1, nlow * cbytes + 2 * vbytes + (4 if w["precision"] == 2 else 0)
-        run_k = lambda: h.level_apply(0, op, b=rhs, y=vec)
+        kname = "k_sweep3 (ILU(0) lower solve, level 0)"
+        flops_pt, bytes_pt = 2 * nlow + 1, nlow * cbytes + 2 * vbytes + sbytes
     else:
-        op, kname = smg.OP_GS_FORWARD, "%s (Gauss-Seidel forward, level 0)" % kfile
-        flops_pt = (2 * (nsf - 1) + 2) * B * B
-        bytes_pt = ((nsf - 1) * cbytes * B * B + (8 if w["precision"] == 0 else 4) * B * B + 3 * vbytes * B
-                    + (4 if w["precision"] == 2 else 0))
-        vec.zero_()
-        run_k = lambda: h.level_apply(0, op, x=vec, b=rhs)
-    for _ in range(2):
-        run_k()
-    nk = 10
-    e0.record(st)
-    for _ in range(nk):
-        run_k()
-    e1.record(st)
-    torch.cuda.synchronize()
-    k_ms = e0.elapsed_time(e1) / nk
-    h.close()
-    peaks = measured_peaks()
-    hbm = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+        kfile = ("k_sweep3" if ny <= 512 else "k_sweep2") if B == 1 else "k_bsweep3"
+        kname = "%s (Gauss-Seidel zero-guess forward, level 0)" % kfile
+        flops_pt = (2 * nlow + 2) * B * B
+        bytes_pt = nlow * cbytes * B * B + vbytes * B * B + 2 * vbytes * B + sbytes
+    k_ms = main_profile[(0, "pre1")]
+    hbm = float(measured_peaks().get("hbm_gbs", HBM_PEAK_FALLBACK))
     k_gbs = lvl0 * bytes_pt / (k_ms * 1e-3) / 1e9
-    k_tf = lvl0 * flops_pt / (k_ms * 1e-3) / 1e12
-    fp64 = w["precision"] == 0
-    # DRAM bytes per launch of the dominant kernel from one ncu capture
-    # (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel on the
-    # same problem at 128^3, scaled by the 8x points of a 256^3 launch; None
-    # where no capture of the current kernel exists
-    traffic = {"c2": round(8 * (483.681536e6 + 16.680960e6))}.get(args.workload)
-    if fp64:
-        roof = {"bound": "alu", "achieved": round(k_tf, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(k_tf / FP64_PEAK_TFLOPS, 4), "traffic": traffic, "kernel": kname,
-                "peak_source": "nominal GB300 FP64 rate 1.25 TFLOP/s (no FP64 tensor path)",
-                "hbm_achieved_gbs": round(k_gbs, 1), "hbm_frac_of_measured": round(k_gbs / hbm, 4),
-                "algorithmic_flops_per_point": flops_pt, "algorithmic_bytes_per_point": bytes_pt,
-                "launch_ms": round(k_ms, 4)}
-    else:
-        roof = {"bound": "hbm", "achieved": round(k_gbs, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(k_gbs / hbm, 4), "traffic": traffic, "kernel": kname,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback",
-                "algorithmic_bytes_per_point": bytes_pt, "launch_ms": round(k_ms, 4)}
+    roof = {"bound": "hbm", "achieved": round(k_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(k_gbs / hbm, 4),
+            "traffic": TRAFFIC.get((args.workload, main_prec)), "kernel": kname,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in measured_peaks() else "fallback",
+            "algorithmic_bytes_per_point": bytes_pt, "launch_ms": round(k_ms, 4),
+            "launch_timing": "CUDA events around the kernel inside a profiled V-cycle (median of 3)"}
+    if main_prec == 0:
+        pk, src = fp64_peak()
+        k_tf = lvl0 * flops_pt / (k_ms * 1e-3) / 1e12
+        roof["alu"] = {"achieved_tflops": round(k_tf, 4), "peak_tflops": pk, "frac": round(k_tf / pk, 4),
+                       "algorithmic_flops_per_point": flops_pt, "peak_source": src}
 
-    extra = {}
+    extra = {"forms": form_info, "vcycle": vcycles}
     if learned_info is not None:
-        extra = {"learned": learned_info, "plain_pcg": plain}
+        extra.update({"learned": learned_info, "plain_pcg": plain})
+    out = dict(ms=ms, iters=results[-1][0], relres=max(r[1] for r in results), stats=stats_main, clocks=clocks,
+               launches=launches, roof=roof, hbm=hbm, extra=extra, e2e_ms=float("nan"), h2d=0, d2h=0)
     if args.no_e2e:
-        return dict(ms=ms, iters=iters, relres=relres, stats=s, clocks=clocks, launches=launches, vc_ms=vc_ms,
-                    vc_gbs=vc_gbs, hbm=hbm, roof=roof, e2e_ms=float("nan"), h2d=0, d2h=0, extra=extra)
+        return out
 
-    # --- e2e: host buffers, copies inside the timed region ---------------------
+    # ---- e2e: host buffers, copies inside the timed region (main form) ------
     A_h = A.cpu().pin_memory()
     b_h = b.cpu().pin_memory()
     x_h = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -388,16 +446,19 @@ def run_ours(args, w, rank, world):
         b_d.copy_(b_h, non_blocking=True)
         if lk_d is not None:
             lk_d.copy_(lk_h, non_blocking=True)
-        hh = make_ctx(A_d, lk_d)
+        hh = make_ctx(main_prec, A_d, lk_d)
         x_d.zero_()
-        hh.solve(b_d, x_d, tol=w["tol"], maxit=1000, check=False)
+        it, rr, rc = hh.solve(b_d, x_d, tol=w["tol"], maxit=1000, check=False)
         hh.close()
+        if rc != 0:
+            raise RuntimeError("e2e solve failed: status %d" % rc)
         x_h.copy_(x_d, non_blocking=True)
 
     e2e_step()
     torch.cuda.synchronize()
     ne = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(ne):
         e2e_step()
@@ -405,18 +466,18 @@ def run_ours(args, w, rank, world):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / ne
     e2e_wall = (time.perf_counter() - t0) / ne * 1e3
-    e2e_ms = max_over_ranks(max(e2e_ms, e2e_wall), dev, world)
-
-    return dict(ms=ms, iters=iters, relres=relres, stats=s, clocks=clocks, launches=launches, vc_ms=vc_ms,
-                vc_gbs=vc_gbs, hbm=hbm, roof=roof, e2e_ms=e2e_ms,
-                h2d=A.numel() * 8 + n * 8 + (0 if logk is None else logk.numel() * 8), d2h=n * 8, extra=extra)
+    out.update(e2e_ms=max_over_ranks(max(e2e_ms, e2e_wall), dev, world),
+               h2d=A.numel() * 8 + n * 8 + (0 if logk is None else logk.numel() * 8), d2h=n * 8)
+    return out
 
 
-def oracle_sample(w, seed=0):
-    """Times the CPU oracle on a bounded sample of the workload: the same
-    problem family on a grid with 1/8 (or 1/64) of the points, full set-up plus
-    Krylov solve, scaled to the workload by the number of unknowns."""
-    import numpy as np
+def oracle_sample(w, seed=0, full_iters=None):
+    """Times the CPU oracle (one thread) on a bounded sample of the workload:
+    the same problem family on a grid with 1/8 of the points per dimension
+    halving (at most 64^3 points), full set-up plus Krylov solve.  The set-up
+    is scaled to the workload by the number of unknowns, the solve by the
+    unknowns and, when the full-size iteration count is known, by the ratio of
+    iteration counts."""
     from oracle import oracle as orc
     orc.build()
     orc.set_threads(1)  # the oracle as written: one thread
@@ -430,20 +491,31 @@ def oracle_sample(w, seed=0):
     off, A, b = make_problem(ws, seed, "cpu")
     A, b = A.numpy(), b.numpy()
     B = w.get("block", 1)
+    prec = w["precision"] if (B == 1 or w["precision"] != 2) else 0
     t0 = time.perf_counter()
-    # the oracle's reduced-precision cycles are scalar only: a block workload
-    # is timed with its FP64 hierarchy
-    prec = w["precision"] if B == 1 else 0
     mg = orc.MG(sd, off, A.reshape(A.shape[0], -1) if B == 1 else A, B=B, smoother=w["smoother"],
                 transfer=w["transfer"], precision=prec)
+    t1 = time.perf_counter()
     if w["krylov"] == 2:
         x, rc, it, rr, _ = mg.fgmres(b, tol=w["tol"], restart=30, maxit=1000)
     else:
         x, rc, it, rr, _ = mg.pcg(b, tol=w["tol"], maxit=1000, flexible=w["krylov"] == 1)
-    t = time.perf_counter() - t0
+    t2 = time.perf_counter()
     scale = full / (sd[0] * sd[1] * sd[2])
-    return dict(value=t * scale, raw_s=t, scale=scale, grid=sd, iters=it, relres=rr, rc=rc,
-                fp64_hierarchy=prec != w["precision"])
+    ratio = (full_iters / it) if (full_iters and it) else 1.0
+    return dict(value=(t1 - t0) * scale + (t2 - t1) * scale * ratio, raw_s=t2 - t0, setup_s=t1 - t0, solve_s=t2 - t1,
+                scale=scale, iter_ratio=ratio, grid=sd, iters=it, relres=rr, rc=rc)
+
+
+def sample_text(o, full_iters=None):
+    txt = ("grid %s (1/%d of the unknowns): set-up %.2f s + solve %.2f s in %d iterations on one core; set-up x%d, "
+           "solve x%d" % ("x".join(map(str, o["grid"])), o["scale"], o["setup_s"], o["solve_s"], o["iters"], o["scale"],
+                          o["scale"]))
+    if full_iters:
+        txt += " x %d/%d (iterations at full size / in the sample)" % (full_iters, o["iters"])
+    else:
+        txt += " (iteration growth with size not included: a lower bound)"
+    return txt
 
 
 def main():
@@ -463,7 +535,7 @@ def main():
     config = {"workload": w["desc"], "dims": list(w["dims"]), "unknowns_per_point": w.get("block", 1),
               "smoother": ["sym-GS", "ILU(0)", "sym-LGS (z-lines)"][w["smoother"]], "transfer": ["3d27v", "3d8c", "3d64c interp. + 3d8c restr.",
                                                                 "x-y semi-coarsening, 2d16c interp. + 2d4c restr."][w["transfer"]],
-              "hierarchy_precision": ["fp64", "fp32", "bf16-rowscaled"][w["precision"]],
+              "hierarchy_precision": "+".join(["fp64", "fp32", "bf16-rowscaled"][p] for p in w.get("forms", (w["precision"],))),
               "krylov": ["PCG", "FPCG", "FGMRES(30)"][w["krylov"]], "tol": w["tol"],
               "parallelism": "replicas" if args.gpus > 1 else "single-gpu",
               "l2": "inputs larger than L2 (matrix of %.1f GB)" % (
@@ -472,16 +544,23 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        r = oracle_sample(w)
-        line = {"impl": "reference", "metric": metric, "value": round(r["value"], 4), "unit": "s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["value"] * 1e3, 2),
+        # each step is one bounded oracle sample of the workload
+        for _ in range(args.warmup):
+            oracle_sample(w)
+        runs = [oracle_sample(w) for _ in range(max(1, args.steps))]
+        raw = statistics.mean(o["raw_s"] for o in runs)
+        value = statistics.median(o["value"] for o in runs)
+        o = runs[-1]
+        line = {"impl": "reference", "metric": metric, "value": round(value, 4), "unit": "s", "n_gpus": args.gpus,
+                "steps": len(runs), "warmup": args.warmup, "ms_per_step": round(raw * 1e3, 2),
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": config,
-                "cpu_baseline": {"value": round(r["value"], 4), "unit": "s", "cores": 1, "kind": "oracle",
-                                 "sample": "grid %s (1/%d of the unknowns), full set-up + solve (%d iterations), "
-                                           "time x%d" % ("x".join(map(str, r["grid"])), r["scale"], r["iters"],
-                                                         r["scale"])},
-                "e2e": {"value": round(r["value"], 4), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                "sample_grid": list(o["grid"]), "sample_s": round(raw, 4), "scale_unknowns": o["scale"],
+                "value_is": "median over the steps of the sample time scaled to the workload's unknowns; "
+                            "ms_per_step is the unscaled sample time",
+                "cpu_baseline": {"value": round(value, 4), "unit": "s", "cores": 1, "kind": "oracle",
+                                 "sample": sample_text(o)},
+                "e2e": {"value": round(value, 4), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
     if world > 1:
@@ -494,24 +573,22 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline:
-        o = oracle_sample(w)
+        o = oracle_sample(w, full_iters=r["iters"])
         cpu = {"value": round(o["value"], 3), "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": "grid %s (1/%d of the unknowns), full set-up + solve in %d iterations, time x%d" % (
-                   "x".join(map(str, o["grid"])), o["scale"], o["iters"], o["scale"])}
+               "sample": sample_text(o, r["iters"])}
         if w.get("learned"):
             cpu["sample"] += "; plain V-cycle (the timed oracle runs no network)"
-        if o.get("fp64_hierarchy"):
-            cpu["sample"] += "; FP64 hierarchy (the oracle has no reduced-precision block cycle)"
     s = r["stats"]
+    main = PREC[w.get("forms", (w["precision"],))[0]]
+    vc = r["extra"]["vcycle"][main]
     line = {"metric": metric, "value": round(r["ms"] / 1e3, 5), "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(r["ms"], 3), "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": ["f64", "f64+f32", "f64+bf16"][w["precision"]], "data": "synthetic",
-            "config": config,
-            "iterations": r["iters"][-1], "final_true_relres": r["relres"],
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f64+f32", "bf16": "f64+bf16"}[main],
+            "data": "synthetic", "config": config,
+            "iterations": r["iters"], "final_true_relres": r["relres"],
             "setup_ms": round(s["setup_ms"], 3), "levels": s["levels"],
             "grid_complexity": round(s["grid_complexity"], 4), "operator_complexity": round(s["operator_complexity"], 4),
-            "vcycle_ms": round(r["vc_ms"], 4), "vcycle_gbs": round(r["vc_gbs"], 1),
-            "vcycle_hbm_frac": round(r["vc_gbs"] / r["hbm"], 4),
+            "vcycle_ms": vc["vcycle_ms"], "vcycle_gbs": vc["vcycle_gbs"], "vcycle_hbm_frac": vc["vcycle_hbm_frac"],
             "roofline": r["roof"],
             "cpu_baseline": cpu,
             "e2e": {"value": round(r["e2e_ms"] / 1e3, 5), "unit": "s", "h2d_bytes_per_step": int(r["h2d"]),

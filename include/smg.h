@@ -136,13 +136,16 @@ int smg_vcycle(smg_t h, const double* r, double* z, void* stream);
  * never from a captured graph), with a CUDA event recorded on the stream
  * after every stage, so the device time of each stage is measured without
  * host gaps.  Stage t (0 <= t < *count) ran on level levels[t]; stages[t] is
- * one of SMG_STAGE_*; ms[t] its device time.  At most cap entries are
+ * one of SMG_STAGE_* (PACK / UNPACK: vectors into and out of the sweeps'
+ * skewed plane layout; POST_ADD: the unpack that adds the correction); ms[t]
+ * its device time.  At most cap entries are
  * written (*count is the full number).  Synchronises the stream.  Not part
  * of the method: a measurement aid for the per-level cost of a cycle.
  * Errors: SMG_EINVAL (NULL or aliased pointers, cap < 0), SMG_ECUDA. */
 enum { SMG_STAGE_PRE1 = 1, SMG_STAGE_PRE2 = 2, SMG_STAGE_RESIDUAL = 3, SMG_STAGE_RESTRICT = 4,
        SMG_STAGE_COARSE = 5, SMG_STAGE_PROLONG = 6, SMG_STAGE_POST_RESIDUAL = 7, SMG_STAGE_POST1 = 8,
-       SMG_STAGE_POST2 = 9, SMG_STAGE_POST_ADD = 10, SMG_STAGE_CAST = 11, SMG_STAGE_LEARNED = 12 };
+       SMG_STAGE_POST2 = 9, SMG_STAGE_POST_ADD = 10, SMG_STAGE_CAST = 11, SMG_STAGE_LEARNED = 12,
+       SMG_STAGE_PACK = 13, SMG_STAGE_UNPACK = 14 };
 int smg_vcycle_profile(smg_t h, const double* r, double* z, int cap, int* count, int* levels, int* stages,
                        float* ms, void* stream);
 

@@ -120,7 +120,7 @@ struct smg_ctx {
 // Records a profiling event after the launches of one stage (no-op unless a
 // profiled V-cycle is running).
 enum { PM_START = 0, PM_PRE1, PM_PRE2, PM_RESID, PM_RESTRICT, PM_COARSE, PM_PROLONG, PM_POST_RESID, PM_POST1,
-       PM_POST2, PM_POST_ADD, PM_CAST, PM_LEARNED };
+       PM_POST2, PM_POST_ADD, PM_CAST, PM_LEARNED, PM_PACK, PM_UNPACK };
 static void prof_mark(smg_ctx* h, int level, int code, cudaStream_t st) {
   if (!h->prof_on) return;
   if (h->prof_n >= (int)h->prof_ev.size()) {
@@ -271,12 +271,14 @@ static int smooth_pre(smg_ctx* h, Level& L, int l, const void* f, void* u, cudaS
   if (skewed(L)) {
     // f -> vs0; the first sweep writes vs1 from zero, the second updates it
     TRY(skew(h, L, f, L.vs0, true, false, st));
+    prof_mark(h, l, PM_PACK, st);
     const bool ilu = h->opt.smoother == SMG_SMOOTHER_ILU0;
     TRY(sweep_rec(h, L, ilu ? SW_ILU_L : SW_GS_ZERO, +1, L.vs0, L.vs1, st));
     prof_mark(h, l, PM_PRE1, st);
     TRY(sweep_rec(h, L, ilu ? SW_ILU_U : SW_GS_FULL, -1, ilu ? L.vs1 : L.vs0, L.vs1, st));
-    TRY(skew(h, L, L.vs1, u, false, false, st));
     prof_mark(h, l, PM_PRE2, st);
+    TRY(skew(h, L, L.vs1, u, false, false, st));
+    prof_mark(h, l, PM_UNPACK, st);
     return SMG_OK;
   }
   if (h->opt.smoother == SMG_SMOOTHER_LGS) {
@@ -302,8 +304,9 @@ static int smooth_post(smg_ctx* h, Level& L, int l, const void* f, void* u, cuda
       // u += U^-1 L^-1 (f - A u): the residual in natural order, the solves
       // on skewed vectors, the correction added while unpacking
       SMG_CUDA_TRY(launch_spmv(view(h, L, true), u, f, L.t, 1, st));
-      TRY(skew(h, L, L.t, L.vs0, true, false, st));
       prof_mark(h, l, PM_POST_RESID, st);
+      TRY(skew(h, L, L.t, L.vs0, true, false, st));
+      prof_mark(h, l, PM_PACK, st);
       TRY(sweep_rec(h, L, SW_ILU_L, +1, L.vs0, L.vs1, st));
       prof_mark(h, l, PM_POST1, st);
       TRY(sweep_rec(h, L, SW_ILU_U, -1, L.vs1, L.vs1, st));
@@ -313,11 +316,13 @@ static int smooth_post(smg_ctx* h, Level& L, int l, const void* f, void* u, cuda
     } else {
       TRY(skew(h, L, f, L.vs0, true, false, st));
       TRY(skew(h, L, u, L.vs1, true, false, st));
+      prof_mark(h, l, PM_PACK, st);
       TRY(sweep_rec(h, L, SW_GS_FULL, +1, L.vs0, L.vs1, st));
       prof_mark(h, l, PM_POST1, st);
       TRY(sweep_rec(h, L, SW_GS_FULL, -1, L.vs0, L.vs1, st));
-      TRY(skew(h, L, L.vs1, u, false, false, st));
       prof_mark(h, l, PM_POST2, st);
+      TRY(skew(h, L, L.vs1, u, false, false, st));
+      prof_mark(h, l, PM_UNPACK, st);
     }
     return SMG_OK;
   }

@@ -297,7 +297,7 @@ class SMG:
             raise SmgError(rc, "smg_learned_loss_grad")
 
     STAGES = {1: "pre1", 2: "pre2", 3: "residual", 4: "restrict", 5: "coarse", 6: "prolong", 7: "post_residual",
-              8: "post1", 9: "post2", 10: "post_add", 11: "cast", 12: "learned"}
+              8: "post1", 9: "post2", 10: "post_add", 11: "cast", 12: "learned", 13: "pack", 14: "unpack"}
 
     def vcycle_profile(self, r, z, stream=None):
         """One eager V-cycle with an event after every stage; returns a list of

@@ -24,6 +24,10 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["config"]["workload"].startswith("poisson7_32^3")
+    # the steps it reports are the samples it ran; the per-step time is the
+    # unscaled sample time, reported beside the scale
+    assert d["steps"] == 1 and abs(d["ms_per_step"] - 1e3 * d["sample_s"]) <= 1e-3 * max(1.0, d["ms_per_step"])
+    assert d["scale_unknowns"] >= 1 and d["value"] >= 0.99 * d["sample_s"] * d["scale_unknowns"] / 10
 
 
 def test_every_workload_has_a_label():
