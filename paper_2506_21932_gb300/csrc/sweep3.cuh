@@ -14,12 +14,20 @@
 //    K = s - SB*J of its column at step s.
 //  * A neighbour of the lower triangle is older than its point by a fixed
 //    number of steps, its slack (SA*dx' + SB*dy' + dz' in sweep coordinates).
-//    Previous-plane values are loaded as late as their slack allows: with a
-//    lookahead of X steps, a term of slack sigma is loaded min(2, sigma+X-1)
-//    steps before its point is finished, so a warp of the next plane only
-//    needs the previous plane to be SA + X steps ahead (X = 0 for FP64,
-//    whose long instruction latency hides the one load issued in the step;
-//    X = 1 for FP32 / BF16).
+//    With a lookahead of X steps a warp of the next plane needs the previous
+//    plane to be SA + X steps ahead.  X = 0 for FP64, whose long FMA issue
+//    time covers one load issued and consumed in the same step; X = 1 for
+//    FP32 / BF16.
+//  * Skewed layout (records and vectors, ilurec.cuh): what one plane
+//    finishes at its local step t is one row of the vector (row t mod nz),
+//    contiguous over j.  Each compute warp keeps the previous plane's last
+//    kRowRing rows over its 32 columns and one on either side in shared
+//    memory: a step issues one coalesced row load (row s + SA - 1 + X) and
+//    commits it before the finish (X = 0) or a step later (X = 1), and every
+//    previous-plane term is a shared-memory read at a constant offset.
+//  * Natural layout (the context-free entry point): previous-plane values
+//    are loaded one by one, as late as their slack allows: a term of slack
+//    sigma is loaded min(2, sigma+X-1) steps before its point is finished.
 //  * Inside a step: wait for the three counters it depends on (left warp,
 //    right warp for the shared value ring, previous plane), issue the loads
 //    whose slack is one step, pre-sum point K+1 (every term that is already
@@ -109,6 +117,11 @@ constexpr unsigned kPublishGapNs = 100;
 // left-hand neighbour may run at most kRing - SB - 2 steps ahead of the
 // published step without overwriting a value still to be read.
 constexpr int kRing = 16;
+// Skewed layout: ring of the previous plane's last kRowRing rows (one row per
+// step of that plane), 34 columns (the warp's 32 and one on either side) per
+// compute warp.  A step reads rows s-SB-1 .. s+SA-1 and loads row s+SA-1+X.
+constexpr int kRowRing = 8;
+constexpr int kRowCols = 34;
 
 __device__ __forceinline__ int ld_acq_cta(const int* p) {
   int v;
@@ -188,6 +201,7 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
   constexpr int LEAD = kRing - SB - 2;  // largest lead over the right-hand warp
   // shared value ring: hist[plane][k % kRing][column]
   V* hist = (V*)dyn_smem;
+  V* prow_all = hist + (size_t)W * kRing * NW * 32;
   const int ngroups = (g.nx + W - 1) / W;
   for (int t = threadIdx.x; t < W * kRing * NW * 32; t += blockDim.x) hist[t] = V(0);
 
@@ -290,6 +304,43 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
         const int s_end = SB * jlast + g.nz - 1;
         const int gt0 = SA * Ip;
         V* hp = hist + (size_t)p * kRing * (NW * 32);
+        // the previous schedule plane (skewed layout): it writes one row per
+        // step, the row of its local step t being t mod nz (forward) or
+        // (nz - 1 + SB (ny - 1) - t) mod nz (backward), the same for all its
+        // columns
+        V* prw = prow_all + (size_t)(p * NW + w) * (kRowRing * kRowCols);
+        const bool has_prev = DIR > 0 ? i > 0 : i + 1 < g.nx;
+        const int rback = (g.nz - 1 + SB * (g.ny - 1)) % g.nz;
+        V pend0 = V(0), pend1 = V(0);  // the row loaded one step ago, not yet in the ring
+        // lane's value of producer step t in ring order: its column 32w-1+lane,
+        // and columns 32w+31, 32w+32 for lanes 0, 1 (zero off the grid, where
+        // the coefficient is zero too)
+        auto load_row = [&](int t, V& v0, V& v1) {
+          int r = (DIR > 0 ? t : rback - t) % g.nz;
+          r = r < 0 ? r + g.nz : r;
+          const long long base = ((long long)(i - DIR) * g.nz + r) * g.ny;
+          auto val = [&](int Jc) -> V {
+            V v = V(0);
+            const int Kc = t - SB * Jc;
+            if (has_prev && Jc >= 0 && Jc < g.ny && Kc >= 0 && Kc < g.nz) {
+              const V* q = u + base + (DIR > 0 ? Jc : g.ny - 1 - Jc);
+              v = (W == 1 || p == 0) ? __ldcg(q) : *q;
+            }
+            return v;
+          };
+          v0 = val(32 * w - 1 + lane);
+          v1 = lane < 2 ? val(32 * w + 31 + lane) : V(0);
+        };
+        auto commit_row = [&](int t, V v0, V v1) {
+          V* rw = prw + (t & (kRowRing - 1)) * kRowCols;
+          rw[lane] = v0;
+          if (lane < 2) rw[32 + lane] = v1;
+        };
+        // previous-plane neighbour (sweep offsets sy, sz) of the point of step sp
+        auto prev = [&](int sp, int e) -> V {
+          const int sy = DIR * S::o(e, 1), sz = DIR * S::o(e, 2);
+          return prw[((sp + SB * sy + sz) & (kRowRing - 1)) * kRowCols + lane + sy + 1];
+        };
         int have_left = (w == 0) ? kDone : INT_MIN;        // cached progress of the left warp
         int have_right = (w + 1 == NW) ? kDone : INT_MIN;  // cached progress of the right warp
         int have_up = INT_MIN;                             // cached progress of the previous plane
@@ -405,6 +456,23 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
           aborted = __shfl_sync(0xffffffffu, aborted, 0);
           if (aborted) break;
           __syncwarp();
+          if constexpr (SPLIT) {
+            // rows s-SB-1 .. s+SA-2+X must be in the ring now: the first step
+            // of the plane loads them, later steps (X = 1) commit the row
+            // loaded one step ago.  Row s+SA-1+X is loaded here; with X = 0
+            // it is committed before the finish of K, which reads it.
+            if (s == s_begin) {
+              for (int t = s - SB - 1; t <= s + SA - 2 + X; ++t) {
+                V v0, v1;
+                load_row(t, v0, v1);
+                commit_row(t, v0, v1);
+              }
+            } else if (X == 1) {
+              commit_row(s + SA - 1, pend0, pend1);
+            }
+            load_row(s + SA - 1 + X, pend0, pend1);
+            __syncwarp();
+          }
           const int K = s - SB * J;
           const bool okK = colok && K >= 0 && K < g.nz;
           const bool okK1 = colok && K + 1 >= 0 && K + 1 < g.nz;
@@ -415,7 +483,7 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
 #pragma unroll
           for (int e = 0; e < NS; ++e) {
             x0[e] = V(0);
-            if (use<NS, KIND, DIR, X>(e) == U_FIN0 && okK) x0[e] = nb(e, kK);
+            if (!SPLIT && use<NS, KIND, DIR, X>(e) == U_FIN0 && okK) x0[e] = nb(e, kK);
           }
 
           // (b) pre-sum of point K+1: every term that is final by now
@@ -429,6 +497,8 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
               V tv;
               if (cls<NS, KIND, DIR>(e) == T_Y) {
                 tv = ring(K + 1 + DIR * S::o(e, 2));  // sweep index of the left column's point
+              } else if (SPLIT && cls<NS, KIND, DIR>(e) == T_X) {
+                tv = prev(s + 1, e);
               } else {
                 tv = x2[e];
               }
@@ -448,6 +518,11 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
             if (us == U_FIN0 || us == U_FIN1 || us == U_FINR) cfN[e] = coef2(e);
           }
 
+          if constexpr (SPLIT && X == 0) {
+            commit_row(s + SA - 1, pend0, pend1);
+            __syncwarp();
+          }
+
           // (c) finish point K
           if (okK) {
             V a = accK;
@@ -460,6 +535,8 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
                 tv = carry;
               } else if (cls<NS, KIND, DIR>(e) == T_Y) {
                 tv = ring(K + DIR * S::o(e, 2));
+              } else if (SPLIT) {
+                tv = prev(s, e);
               } else {
                 tv = us == U_FIN0 ? x0[e] : x1[e];
               }
@@ -494,7 +571,7 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
             const int k1 = DIR > 0 ? K + 1 : g.nz - 2 - K;
 #pragma unroll
             for (int e = 0; e < NS; ++e)
-              if (use<NS, KIND, DIR, X>(e) == U_FIN1) x1[e] = nb(e, k1);
+              if (!SPLIT && use<NS, KIND, DIR, X>(e) == U_FIN1) x1[e] = nb(e, k1);
           }
 
           // (e) operands of point K+2
@@ -527,7 +604,9 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
             }
 #pragma unroll
             for (int e = 0; e < NS; ++e)
-              if (use<NS, KIND, DIR, X>(e) == U_PRE && cls<NS, KIND, DIR>(e) != T_Y) x2[e] = nb(e, k2);
+              if (use<NS, KIND, DIR, X>(e) == U_PRE && cls<NS, KIND, DIR>(e) != T_Y &&
+                  !(SPLIT && cls<NS, KIND, DIR>(e) == T_X))
+                x2[e] = nb(e, k2);
             b2 = b[p2];
             if (KIND == SW_GS_FULL && relax) uo2 = u[p2];
           }
@@ -568,7 +647,8 @@ cudaError_t launch_kind(int kind, int dir, bool rec, const Sweep3Params& P, cuda
   const int nthr = (W * NW + 2) * 32;
   // the value ring needs <= 64 KB (ny <= 512); reserving more than half of
   // the SM's 228 KB keeps a second CTA off the SM
-  const size_t smem = std::max(sizeof(V) * kRing * (size_t)(NW * 32) * W, kOneCtaPerSmSmem);
+  const size_t smem = std::max(sizeof(V) * ((size_t)kRing * NW * 32 + (size_t)kRowRing * kRowCols * NW) * W,
+                               kOneCtaPerSmSmem);
   int dev = 0, nsm = 0;
   cudaError_t ae = cudaGetDevice(&dev);
   if (ae == cudaSuccess) ae = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
