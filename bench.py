@@ -90,11 +90,15 @@ DEFAULT = "c3"
 HBM_PEAK_FALLBACK = 6800.0
 FP64_PEAK_NOMINAL = 1.25  # TFLOP/s, used only when the measured figure is missing
 FP64_PROBE = os.path.join(ROOT, "profiles", "fp64_fma_peak_gb300.txt")
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernel from one ncu capture of the current kernel on the same
-# problem family at a smaller size, scaled by the points of a full launch;
-# None where no capture of the current kernel exists
-TRAFFIC = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per point of the
+# dominant kernel, from one ncu capture of the current kernel on the same
+# problem family at a smaller size (the traffic grows with the points); keyed
+# by (smoother, stencil points, precision).  Absent where no capture of the
+# current kernel exists.
+TRAFFIC_PER_POINT = {
+    # k_sweep3 ILU lower solve, FP64, 27 points: 267.9 MB for 128^3
+    (1, 27, 0): (267.864e6 / 128 ** 3, "profiles/k_sweep3_ilu_lower_aniso27_128cubed.md"),
+}
 
 
 PREC = {0: "fp64", 1: "fp32", 2: "bf16"}
@@ -412,16 +416,28 @@ def run_ours(args, w, rank, world):
     k_ms = main_profile[(0, "pre1")]
     hbm = float(measured_peaks().get("hbm_gbs", HBM_PEAK_FALLBACK))
     k_gbs = lvl0 * bytes_pt / (k_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": round(k_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(k_gbs / hbm, 4),
-            "traffic": TRAFFIC.get((args.workload, main_prec)), "kernel": kname,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in measured_peaks() else "fallback",
-            "algorithmic_bytes_per_point": bytes_pt, "launch_ms": round(k_ms, 4),
-            "launch_timing": "CUDA events around the kernel inside a profiled V-cycle (median of 3)"}
+    tr = TRAFFIC_PER_POINT.get((w["smoother"], nsf, main_prec)) if B == 1 else None
+    traffic = None if tr is None else round(tr[0] * lvl0)
+    hbm_roof = {"achieved": round(k_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(k_gbs / hbm, 4),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in measured_peaks()
+                else "fallback", "algorithmic_bytes_per_point": bytes_pt}
+    common = {"traffic": traffic, "kernel": kname, "launch_ms": round(k_ms, 4),
+              "launch_timing": "CUDA events around the kernel inside a profiled V-cycle (median of 3)"}
+    if tr is not None:
+        common["traffic_source"] = "ncu capture of the same kernel at a smaller size (%s), scaled by the points" % tr[1]
     if main_prec == 0:
+        # FP64: the binding roof is the FP64 pipe whenever its time at the
+        # measured rate exceeds the bytes' time at the measured bandwidth
         pk, src = fp64_peak()
         k_tf = lvl0 * flops_pt / (k_ms * 1e-3) / 1e12
-        roof["alu"] = {"achieved_tflops": round(k_tf, 4), "peak_tflops": pk, "frac": round(k_tf / pk, 4),
-                       "algorithmic_flops_per_point": flops_pt, "peak_source": src}
+        alu_roof = {"achieved": round(k_tf, 4), "peak": pk, "unit": "TFLOP/s", "frac": round(k_tf / pk, 4),
+                    "peak_source": src, "algorithmic_flops_per_point": flops_pt}
+        if flops_pt / (pk * 1e12) > bytes_pt / (hbm * 1e9):
+            roof = dict({"bound": "alu"}, **alu_roof, **common, hbm=hbm_roof)
+        else:
+            roof = dict({"bound": "hbm"}, **hbm_roof, **common, alu=alu_roof)
+    else:
+        roof = dict({"bound": "hbm"}, **hbm_roof, **common)
 
     extra = {"forms": form_info, "vcycle": vcycles}
     if learned_info is not None:

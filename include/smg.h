@@ -68,13 +68,13 @@ enum { SMG_KRYLOV_PCG = 0, SMG_KRYLOV_FPCG = 1, SMG_KRYLOV_FGMRES = 2 };
  *                    whose Thomas pivots are not all positive gives
  *                    SMG_EBREAKDOWN.
  *  transfer   [FW27V] vertex full weighting: coarse I on fine 2I+1, trilinear
- *                    P and R = P^T/8 (Table 3 pattern 3d27v); PC8C: cell
+ *                    P and R = P^T/8 (Table 2 pattern 3d27v); PC8C: cell
  *                    piecewise constant, R(I,u)=1 on u in 2I+{0,1}^3, P = R^T
- *                    (Table 3 pattern 3d8c); C64C: the same 3d8c restriction
+ *                    (Table 2 pattern 3d8c); C64C: the same 3d8c restriction
  *                    with cell-centred trilinear interpolation, per dimension
  *                    3/4 from the fine cell's own coarse cell and 1/4 from
  *                    the next one on its side, coarse cells off the grid
- *                    dropped (Table 3 columns 3d8c / A / 3d64c; the Table 8
+ *                    dropped (Table 2 columns 3d8c / A / 3d64c; the Table 8
  *                    settings of rhd-3T and solid-3D).  R is not a multiple
  *                    of P^T, so the coarse operators and the V-cycle are
  *                    nonsymmetric: use FPCG or FGMRES (PCG is accepted; the
@@ -269,7 +269,7 @@ int smg_derive_chains(int dim, int nr, const int* roff, int na, const int* aoff,
 
 /* Host-only: the Galerkin chain table the hierarchy set-up uses for one
  * transfer (SMG_TRANSFER_*) on a fine mask of nstencil offsets (int[3] each,
- * any order).  Returns the number of chains (Table 3 counts them: 1216 for
+ * any order).  Returns the number of chains (Table 2 counts them: 1216 for
  * C64C on 19 points, 1728 on 27) and writes the coarse mask size to
  * *ncoarse if it is not NULL; -1 for an unknown transfer or a mask the
  * derivation rejects.  No GPU is used. */

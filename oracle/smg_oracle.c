@@ -369,7 +369,7 @@ void orc_ilu0_apply(const int d[3], int ns, const int* off, const double* LU, co
 }
 
 /* ------------------------------------------------------------------------- */
-/* Grid transfers (Sec. 2 V-cycle; Table 3 patterns 3d27v, 3d8c and 3d64c)  */
+/* Grid transfers (Sec. 2 V-cycle; Table 2 patterns 3d27v, 3d8c and 3d64c)  */
 /* ------------------------------------------------------------------------- */
 /* Transfer 0 = vertex full weighting: coarse point I sits on fine point 2I+1;
  *   P(v,J) = prod_d w(v_d - (2J_d+1)), w(0)=1, w(+-1)=1/2 (trilinear, 3d27v),
@@ -377,7 +377,7 @@ void orc_ilu0_apply(const int d[3], int ns, const int* off, const double* LU, co
  * Transfer 1 = cell piecewise constant 3d8c: R(I,u) = 1 for u in 2I+{0,1}^3,
  *   P = R^T.
  * Transfer 2 = cell-centred trilinear interpolation 3d64c with the 3d8c
- *   restriction of transfer 1 (Table 3 columns 3d8c / A / 3d64c; the
+ *   restriction of transfer 1 (Table 2 columns 3d8c / A / 3d64c; the
  *   interpolation of the Table 8 settings for rhd-3T and solid-3D).  Coarse
  *   cell J covers fine cells 2J and 2J+1 in every dimension; a fine cell
  *   centre lies a quarter of a coarse cell from the centre of its own coarse

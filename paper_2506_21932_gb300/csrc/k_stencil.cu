@@ -1,5 +1,5 @@
 // Point-parallel stencil kernels: SG-DIA SpMV / residual (Sec. 6.1.1), grid
-// transfers (Sec. 2 V-cycle; Table 3 patterns 3d27v, 3d8c and 3d64c, and the
+// transfers (Sec. 2 V-cycle; Table 2 patterns 3d27v, 3d8c and 3d64c, and the
 // 2d4c / 2d16c pair of x-y semi-coarsening), precision
 // casts and lowering, diagonal inverses and the dense coarsest level.
 #include "ilurec.cuh"

@@ -54,7 +54,7 @@ def _zero_offgrid(A, dims, offsets):
 
 def laplace7(dims, device="cpu"):
     """7-point finite-difference Laplacian (-Delta u) with homogeneous Dirichlet
-    boundary, unit spacing: diagonal 6, neighbours -1 (Table 2 'Laplace')."""
+    boundary, unit spacing: diagonal 6, neighbours -1 (Table 3 'Laplace')."""
     dims = tuple(int(t) for t in dims)
     n = dims[0] * dims[1] * dims[2]
     A = torch.full((n, 7), -1.0, dtype=torch.float64, device=device)

@@ -42,7 +42,7 @@ def test_strerror_covers_every_status(smg):
 
 
 # ----------------------------------------------------------------------------
-# Symbolic chain derivation (Sec. 4.3, Eq. 5-10, Table 3, Listing 1)
+# Symbolic chain derivation (Sec. 4.3, Eq. 5-10, Table 2, Listing 1)
 # ----------------------------------------------------------------------------
 
 def pattern(name):
@@ -67,7 +67,7 @@ def test_chain_counts_match_table3(smg):
 
 def test_chain_counts_of_the_build_combinations(smg):
     """The combinations the hierarchy uses: 3d27v on a 7-point fine matrix and
-    on its 27-point coarse matrices, 3d8c on 7 points (all 56 chains of Table 3)."""
+    on its 27-point coarse matrices, 3d8c on 7 points (all 56 chains of Table 2)."""
     assert len(smg.derive_chains(pattern("3d27v"), pattern("3d7"), pattern("3d27v"))) == 725
     assert len(smg.derive_chains(pattern("3d8c"), pattern("3d27"), pattern("3d8c"))) == 216
     # 3d8c keeps 7 points: only the 7 face/centre coarse offsets are reached
@@ -138,7 +138,7 @@ def test_setup_rejects_bad_arguments(smg):
 
 def test_setup_chain_tables_of_every_transfer(smg):
     """The chain tables the hierarchy set-up builds (product host code):
-    Table 3's 1216 and 1728 chains for 3d8c / 3d19 / 3d64c and 3d8c / 3d27 /
+    Table 2's 1216 and 1728 chains for 3d8c / 3d19 / 3d64c and 3d8c / 3d27 /
     3d64c, the vertex and piecewise-constant pairs, and the x-y
     semi-coarsening pair (per dimension 2 x 2 = 4 matching (r, q) pairs in x
     and y for every stencil entry, 1 in z: 16 chains per fine entry), each

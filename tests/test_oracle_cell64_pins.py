@@ -1,5 +1,5 @@
 """Pins of the oracle's cell-centred transfer pair: 3d64c (trilinear, cell
-centred) interpolation with 3d8c restriction, the combination of Table 3's
+centred) interpolation with 3d8c restriction, the combination of Table 2's
 columns 3d8c / 3d19 / 3d64c and 3d8c / 3d27 / 3d64c and of the Table 8
 settings for rhd-3T and solid-3D.  Each pin checks the oracle against
 something it does not compute itself: exactness on linear functions, dense

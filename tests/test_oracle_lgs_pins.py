@@ -121,7 +121,7 @@ def test_lgs_vcycle_is_symmetric_for_spd(orc):
 def test_lgs_wins_on_z_aligned_anisotropy(orc):
     """Strong coupling along the lines (k_z = 1, k_x = k_y = 1e-3): the line
     smoother removes the anisotropy that point GS cannot (cf. the LGS column
-    of Table 9), and it stays competitive on the isotropic Laplacian."""
+    of Table 6), and it stays competitive on the isotropic Laplacian."""
     d = (24, 24, 24)
     A = I.q1_aniso27(d, 1, aniso=(1e-3, 1e-3, 1.0)).numpy()
     b = I.rhs(24 ** 3, 4).numpy()

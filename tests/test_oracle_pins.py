@@ -91,7 +91,7 @@ def test_dense_assembly_by_hand(orc):
 
 
 def test_laplace_condition_number_closed_form():
-    """Table 2 lists cond ~2e4 for Laplace at 16.8M dof (256^3); the closed form
+    """Table 3 lists cond ~2e4 for Laplace at 16.8M dof (256^3); the closed form
     lambda_max/lambda_min of the 7-point operator on 256^3 is ~2.7e4, the same
     order (the printed figure is an estimate)."""
     n = 256
@@ -313,7 +313,7 @@ def test_rap_laplace_closed_form_kronecker_sum(orc):
 
 def test_rap_cell_transfer_keeps_7pt_laplacian_times_4(orc):
     """3d8c restriction and interpolation of the 7-point Laplacian: the coarse
-    operator is 4 x the same 7-point stencil in the interior (Table 3, 3d8c/
+    operator is 4 x the same 7-point stencil in the interior (Table 2, 3d8c/
     3d7/3d8c keeps the pattern; Table 5 lists C_O = C_G for oil-4C)."""
     fd = (12, 12, 12)
     A = I.laplace7(fd).numpy()
