@@ -315,9 +315,16 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
         // lane's value of producer step t in ring order: its column 32w-1+lane,
         // and columns 32w+31, 32w+32 for lanes 0, 1 (zero off the grid, where
         // the coefficient is zero too)
-        auto load_row = [&](int t, V& v0, V& v1) {
-          int r = (DIR > 0 ? t : rback - t) % g.nz;
-          r = r < 0 ? r + g.nz : r;
+        auto row_of = [&](int t) -> int {
+          const int r = (DIR > 0 ? t : rback - t) % g.nz;
+          return r < 0 ? r + g.nz : r;
+        };
+        // row_of(t + d) = row_of(t) + step_off(d), reduced once below nz
+        auto step_off = [&](int d) -> int {
+          const int r = (DIR * d) % g.nz;
+          return r < 0 ? r + g.nz : r;
+        };
+        auto load_row = [&](int t, int r, V& v0, V& v1) {
           const long long base = ((long long)(i - DIR) * g.nz + r) * g.ny;
           auto val = [&](int Jc) -> V {
             V v = V(0);
@@ -357,14 +364,6 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
           } else {
             return ((long long)(i + dx) * g.ny + (j + dy)) * g.nz + kk;
           }
-        };
-        // first 16-byte unit of the record of this lane's point kk (skewed
-        // layout); chunk c is at unit + c * ny
-        auto rec_unit = [&](int kk) -> long long {
-          int r = br0 + kk;
-          r = r >= g.nz ? r - g.nz : r;
-          r = r >= g.nz ? r - g.nz : r;
-          return ((long long)i * g.nz + r) * R::CHUNKS * g.ny + j;
         };
 
         // stage 2: operands of point K+2, loaded at step s, pre-summed at s+1.
@@ -414,8 +413,26 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
         // starts zeroed, so a slot read off the grid (coefficient zero) is finite
         auto ring = [&](int kk) -> V { return hp[(kk & (kRing - 1)) * (NW * 32) + (J > 0 ? J - 1 : 0)]; };
 
+        // skewed layout: every vector and record access of step s is in row
+        // rs = row_of(s) (point K), rs + off2 (point K+2), rs + offpf (the
+        // prefetch) or rs + offrow (the previous plane's row), the same for
+        // all lanes; rs advances by one row per step
+        const int off1 = SPLIT ? step_off(1) : 0, off2 = SPLIT ? step_off(2) : 0;
+        const int offpf = SPLIT ? step_off(2 + kPrefetch) : 0, offrow = SPLIT ? step_off(SA - 1 + X) : 0;
+        const long long vbase = (long long)i * g.nz * g.ny + j;                // + row * ny
+        const long long rbase = (long long)i * g.nz * R::CHUNKS * g.ny + j;    // + row * CHUNKS * ny
+        int rs = 0;
+        if constexpr (SPLIT) {
+          rs = row_of(s_begin) - off1;
+          rs = rs < 0 ? rs + g.nz : rs;
+        }
+        auto radd = [&](int r, int off) -> int {
+          r += off;
+          return r >= g.nz ? r - g.nz : r;
+        };
         bool aborted = false;
         for (int s = s_begin; s <= s_end; ++s) {
+          if constexpr (SPLIT) rs = radd(rs, off1);
           // -- dependencies, checked by lane 0 against cached counters
           if (lane == 0) {
             unsigned long long t_start = 0;
@@ -464,13 +481,13 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
             if (s == s_begin) {
               for (int t = s - SB - 1; t <= s + SA - 2 + X; ++t) {
                 V v0, v1;
-                load_row(t, v0, v1);
+                load_row(t, row_of(t), v0, v1);
                 commit_row(t, v0, v1);
               }
             } else if (X == 1) {
               commit_row(s + SA - 1, pend0, pend1);
             }
-            load_row(s + SA - 1 + X, pend0, pend1);
+            load_row(s + SA - 1 + X, radd(rs, offrow), pend0, pend1);
             __syncwarp();
           }
           const int K = s - SB * J;
@@ -550,7 +567,7 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
               r = (FOLD ? a : bK - a) * dK;
               if (KIND != SW_ILU_U && relax) r = (KIND == SW_GS_ZERO) ? wv * r : (V(1) - wv) * uoK + wv * r;
             }
-            u[vslot(0, 0, kK)] = r;
+            u[SPLIT ? vbase + (long long)rs * g.ny : vslot(0, 0, kK)] = r;
             hp[(K & (kRing - 1)) * (NW * 32) + J] = r;
             carry = r;
           }
@@ -578,13 +595,13 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
           const int K2 = K + 2;
           if (colok && K2 >= 0 && K2 < g.nz) {
             const int k2 = DIR > 0 ? K2 : g.nz - 1 - K2;
-            const long long p2 = vslot(0, 0, k2);
+            const long long p2 = SPLIT ? vbase + (long long)radd(rs, off2) * g.ny : vslot(0, 0, k2);
             if constexpr (SPLIT) {
-              const uint4* rp = (const uint4*)P.M + rec_unit(k2);
+              const uint4* rp = (const uint4*)P.M + rbase + (long long)radd(rs, off2) * (R::CHUNKS * g.ny);
 #pragma unroll
               for (int c = 0; c < R::CHUNKS; ++c) q2[c] = __ldg(rp + (long long)c * g.ny);
               if (K2 + kPrefetch < g.nz) {
-                const uint4* pf = (const uint4*)P.M + rec_unit(k2 + DIR * kPrefetch);
+                const uint4* pf = (const uint4*)P.M + rbase + (long long)radd(rs, offpf) * (R::CHUNKS * g.ny);
 #pragma unroll
                 for (int c = 0; c < R::CHUNKS; ++c) prefetch_l2(pf + (long long)c * g.ny);
               }
