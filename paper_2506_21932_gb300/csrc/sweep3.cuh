@@ -433,46 +433,45 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
         bool aborted = false;
         for (int s = s_begin; s <= s_end; ++s) {
           if constexpr (SPLIT) rs = radd(rs, off1);
-          // -- dependencies, checked by lane 0 against cached counters
-          if (lane == 0) {
-            unsigned long long t_start = 0;
-            for (;;) {
-              bool ok = true;
-              if (have_left < s) {
-                have_left = ld_acq_cta(&sh.wdone[p][w - 1]);
-                ok = have_left >= s;
-              }
-              if (ok && have_right < s - LEAD) {
-                have_right = ld_acq_cta(&sh.wdone[p][w + 1]);
-                ok = have_right >= s - LEAD;
-              }
-              if (ok) {
-                // the previous plane's points this warp reads lie in columns
-                // 32w-1 .. 32w+32: warps w-1..w+1, SA + X steps ahead
-                const int need = (p == 0) ? gt0 + s + X : s + SA + X;
+          // -- dependencies, against counters cached in registers.  Every
+          // lane checks them (the same values in all lanes, so the warp does
+          // not diverge); only when the cache is stale do the lanes poll the
+          // shared counters, each with its own acquire load (one broadcast).
+          {
+            // the previous plane's points this warp reads lie in columns
+            // 32w-1 .. 32w+32: warps w-1..w+1, SA + X steps ahead
+            const int need = (p == 0) ? gt0 + s + X : s + SA + X;
+            // the caches agree across lanes in practice; the vote makes the
+            // entry (and the barrier-like votes below) uniform regardless
+            if (__any_sync(0xffffffffu, have_left < s || have_right < s - LEAD || have_up < need)) {
+              unsigned long long t_start = 0;
+              for (;;) {
+                if (have_left < s) have_left = ld_acq_cta(&sh.wdone[p][w - 1]);
+                if (have_right < s - LEAD) have_right = ld_acq_cta(&sh.wdone[p][w + 1]);
                 if (have_up < need) {
                   const int* src = (p == 0) ? sh.avail : sh.wdone[p - 1];
                   int T = kDone;
                   for (int ww = max(w - 1, 0); ww <= min(w + 1, NW - 1); ++ww) T = min(T, ld_acq_cta(&src[ww]));
                   have_up = T;
-                  ok = have_up >= need;
+                }
+                if (have_left >= s && have_right >= s - LEAD && have_up >= need) break;
+                if (ld_acq_cta(&sh.abort)) { aborted = true; break; }
+                const unsigned long long now = globaltimer_ns();
+                if (t_start == 0) t_start = now;
+                else if (now - t_start > P.budget_ns) {
+                  if (lane == 0) {
+                    atomicCAS(P.err, 0, DEV_ERR_TIMEOUT);
+                    st_rel_cta(&sh.abort, 1);
+                  }
+                  aborted = true;
+                  break;
                 }
               }
-              if (ok) break;
-              if (ld_acq_cta(&sh.abort)) { aborted = true; break; }
-              const unsigned long long now = globaltimer_ns();
-              if (t_start == 0) t_start = now;
-              else if (now - t_start > P.budget_ns) {
-                atomicCAS(P.err, 0, DEV_ERR_TIMEOUT);
-                st_rel_cta(&sh.abort, 1);
-                aborted = true;
-                break;
-              }
+              // lanes leave the loop together unless one gave up: agree
+              aborted = __any_sync(0xffffffffu, aborted);
+              if (aborted) break;
             }
           }
-          aborted = __shfl_sync(0xffffffffu, aborted, 0);
-          if (aborted) break;
-          __syncwarp();
           if constexpr (SPLIT) {
             // rows s-SB-1 .. s+SA-2+X must be in the ring now: the first step
             // of the plane loads them, later steps (X = 1) commit the row
