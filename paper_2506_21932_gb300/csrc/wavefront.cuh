@@ -113,26 +113,24 @@ __device__ __forceinline__ void wf_poll(WfShared& sh, const WfCtl& C, int I, int
 
 // Wait of compute warp w before its step s: the left warp has finished s-1
 // and warps w-1..w+1 of the previous plane have reached global time need.
-// have_left / have_up cache the last values seen.  Returns nonzero (in every
-// lane) when the plane is aborted.
+// have_left / have_up cache the last values seen (in every lane).  Every
+// lane checks the caches, so the warp does not diverge; only a stale cache
+// sends the warp into the polling loop, where each lane takes its own
+// acquire load of the same shared word.  Returns nonzero (in every lane)
+// when the plane is aborted.
 __device__ __forceinline__ int wf_wait(WfShared& sh, const WfCtl& C, int w, int s, int need, int& have_left,
                                        int& have_up, int lane) {
   int aborted = 0;
-  if (lane == 0) {
+  if (__any_sync(0xffffffffu, have_left < s || have_up < need)) {
     unsigned long long t_start = 0;
     for (;;) {
-      bool ok = true;
-      if (have_left < s) {
-        have_left = wf_ld_acq_cta(&sh.wdone[w - 1]);
-        ok = have_left >= s;
-      }
-      if (ok && have_up < need) {
+      if (have_left < s) have_left = wf_ld_acq_cta(&sh.wdone[w - 1]);
+      if (have_up < need) {
         int Tm = kWfDone;
         for (int ww = max(w - 1, 0); ww <= min(w + 1, C.NW - 1); ++ww) Tm = min(Tm, wf_ld_acq_cta(&sh.avail[ww]));
         have_up = Tm;
-        ok = have_up >= need;
       }
-      if (ok) break;
+      if (have_left >= s && have_up >= need) break;
       if (wf_ld_acq_cta(&sh.abort_flag)) {
         aborted = 1;
         break;
@@ -140,14 +138,17 @@ __device__ __forceinline__ int wf_wait(WfShared& sh, const WfCtl& C, int w, int 
       const unsigned long long now = globaltimer_ns();
       if (t_start == 0) t_start = now;
       else if (now - t_start > C.budget_ns) {
-        atomicCAS(C.err, 0, DEV_ERR_TIMEOUT);
-        wf_st_rel_cta(&sh.abort_flag, 1);
+        if (lane == 0) {
+          atomicCAS(C.err, 0, DEV_ERR_TIMEOUT);
+          wf_st_rel_cta(&sh.abort_flag, 1);
+        }
         aborted = 1;
         break;
       }
     }
+    aborted = __any_sync(0xffffffffu, aborted) ? 1 : 0;
   }
-  return __shfl_sync(0xffffffffu, aborted, 0);
+  return aborted;
 }
 
 // Step s of warp w is finished (its stores precede the release).
