@@ -163,51 +163,84 @@ __global__ void __launch_bounds__(TPB) k_restrict_pc(Grid f, Grid c, const V* __
   for (int r = 0; r < B; ++r) fc[P * B + r] = acc[r];
 }
 
-// uf += P ec.  For full weighting, a fine coordinate v is either on a coarse
-// point (v odd: weight 1 from J = (v-1)/2) or between two (v even: weights
-// 1/2 from J = v/2 - 1 and J = v/2, the ones off the coarse grid dropped).
+// uf += P ec for full weighting.  Per dimension a fine coordinate v is
+// either on a coarse point (v = 2I + 1: weight 1 from I) or between two
+// (v = 2I + 2: weights 1/2 from I and I + 1, the one off the coarse grid
+// dropped).  One thread owns the fine points 2I + 1 and 2I + 2 of every
+// dimension (I = -1 .. nc - 1; each fine point has exactly one owner) and
+// forms their values separably from the 2 x 2 x 2 coarse values c(I + a):
+// the sums along z, then y, then x, 12 additions for 8 fine points; the
+// weight of a fine point is the power of two 2^-(number of even
+// coordinates), applied exactly in the one fused multiply-add into uf.
 template <typename V, int B>
 __global__ void __launch_bounds__(TPB) k_prolong_fw(Grid f, Grid c, const V* __restrict__ ec, V* __restrict__ uf) {
-  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= f.n) return;
-  int v0, v1, v2;
-  coords(q, f, v0, v1, v2);
-  int lo[3], cnt[3];
-  V w[3][2];
-  const int v[3] = {v0, v1, v2};
+  const int m2 = c.nz + 1, m1 = c.ny + 1;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)(c.nx + 1) * m1 * m2) return;
+  const int I2 = (int)(t % m2) - 1;
+  t /= m2;
+  const int I1 = (int)(t % m1) - 1;
+  const int I0 = (int)(t / m1) - 1;
+  const int I[3] = {I0, I1, I2};
   const int cn[3] = {c.nx, c.ny, c.nz};
+  const int fn[3] = {f.nx, f.ny, f.nz};
+  bool cok[3][2], fok[3][2];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    if (v[d] & 1) {
-      lo[d] = (v[d] - 1) >> 1; cnt[d] = 1; w[d][0] = V(1); w[d][1] = V(0);
-    } else {
-      lo[d] = (v[d] >> 1) - 1; cnt[d] = 2; w[d][0] = V(0.5); w[d][1] = V(0.5);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      cok[d][h] = (unsigned)(I[d] + h) < (unsigned)cn[d];
+      fok[d][h] = (unsigned)(2 * I[d] + 1 + h) < (unsigned)fn[d];
     }
   }
-  V acc[B];
 #pragma unroll
-  for (int r = 0; r < B; ++r) acc[r] = 0;
+  for (int r = 0; r < B; ++r) {
+    V cv[2][2][2];
 #pragma unroll
-  for (int a = 0; a < 2; ++a) {
-    int J0 = lo[0] + a;
-    if (a >= cnt[0] || (unsigned)J0 >= (unsigned)cn[0]) continue;
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      int J1 = lo[1] + b;
-      if (b >= cnt[1] || (unsigned)J1 >= (unsigned)cn[1]) continue;
+      for (int b = 0; b < 2; ++b)
 #pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        int J2 = lo[2] + cc;
-        if (cc >= cnt[2] || (unsigned)J2 >= (unsigned)cn[2]) continue;
-        V wgt = w[0][a] * w[1][b] * w[2][cc];
-        long long P = ((long long)J0 * c.ny + J1) * c.nz + J2;
+        for (int h = 0; h < 2; ++h) {
+          cv[a][b][h] = V(0);
+          if (cok[0][a] && cok[1][b] && cok[2][h])
+            cv[a][b][h] = ec[(((long long)(I0 + a) * c.ny + (I1 + b)) * c.nz + (I2 + h)) * B + r];
+        }
+    // z, then y, then x: index 0 = the odd fine coordinate, 1 = the even one
+    V zs[2][2][2], ys[2][2][2], xs[2][2][2];
 #pragma unroll
-        for (int r = 0; r < B; ++r) acc[r] = fma(wgt, ec[P * B + r], acc[r]);
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        zs[a][b][0] = cv[a][b][0];
+        zs[a][b][1] = cv[a][b][0] + cv[a][b][1];
       }
-    }
-  }
 #pragma unroll
-  for (int r = 0; r < B; ++r) uf[q * B + r] += acc[r];
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int pz = 0; pz < 2; ++pz) {
+        ys[a][0][pz] = zs[a][0][pz];
+        ys[a][1][pz] = zs[a][0][pz] + zs[a][1][pz];
+      }
+#pragma unroll
+    for (int py = 0; py < 2; ++py)
+#pragma unroll
+      for (int pz = 0; pz < 2; ++pz) {
+        xs[0][py][pz] = ys[0][py][pz];
+        xs[1][py][pz] = ys[0][py][pz] + ys[1][py][pz];
+      }
+#pragma unroll
+    for (int px = 0; px < 2; ++px)
+#pragma unroll
+      for (int py = 0; py < 2; ++py)
+#pragma unroll
+        for (int pz = 0; pz < 2; ++pz) {
+          if (!(fok[0][px] && fok[1][py] && fok[2][pz])) continue;
+          const V scale = V(1.0 / (double)(1 << (px + py + pz)));
+          const long long q = ((long long)(2 * I0 + 1 + px) * f.ny + (2 * I1 + 1 + py)) * f.nz + (2 * I2 + 1 + pz);
+          uf[q * B + r] = fma(scale, xs[px][py][pz], uf[q * B + r]);
+        }
+  }
 }
 
 // uf += P ec for the cell-centred trilinear interpolation (3d64c).  Per
@@ -223,15 +256,19 @@ __global__ void __launch_bounds__(TPB) k_prolong_c64(Grid f, Grid c, const V* __
   coords(q, f, v0, v1, v2);
   const int v[3] = {v0, v1, v2};
   const int cn[3] = {c.nx, c.ny, c.nz};
-  int lo[3];
-  V w[3][2];
+  // the weight of coarse cell (lo + (a, b, cc)) is 3^m / 64, m the number
+  // of dimensions whose factor is 3/4 (exact in any precision; selected in
+  // place of the products)
+  auto w64 = [](int m) -> V {
+    return m == 0 ? V(1.0 / 64) : m == 1 ? V(3.0 / 64) : m == 2 ? V(9.0 / 64) : V(27.0 / 64);
+  };
+  int lo[3], hi3[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    if (v[d] & 1) {
-      lo[d] = v[d] >> 1; w[d][0] = V(0.75); w[d][1] = V(0.25);
-    } else {
-      lo[d] = (v[d] >> 1) - 1; w[d][0] = V(0.25); w[d][1] = V(0.75);
-    }
+    // 3/4 from the cell the fine cell lies in: the second of the pair for
+    // an even v, the first for an odd v
+    lo[d] = (v[d] & 1) ? (v[d] >> 1) : (v[d] >> 1) - 1;
+    hi3[d] = (v[d] & 1) ? 0 : 1;
   }
   V acc[B];
 #pragma unroll
@@ -248,7 +285,7 @@ __global__ void __launch_bounds__(TPB) k_prolong_c64(Grid f, Grid c, const V* __
       for (int cc = 0; cc < 2; ++cc) {
         const int J2 = lo[2] + cc;
         if ((unsigned)J2 >= (unsigned)cn[2]) continue;
-        const V wgt = w[0][a] * w[1][b] * w[2][cc];
+        const V wgt = w64((a == hi3[0]) + (b == hi3[1]) + (cc == hi3[2]));
         const long long P = ((long long)J0 * c.ny + J1) * c.nz + J2;
 #pragma unroll
         for (int r = 0; r < B; ++r) acc[r] = fma(wgt, ec[P * B + r], acc[r]);
@@ -716,7 +753,10 @@ cudaError_t launch_restrict(int transfer, Grid f, int B, int pk, const void* rf,
 
 cudaError_t launch_prolong_add(int transfer, Grid f, int B, int pk, const void* ec, void* uf, cudaStream_t st) {
   Grid c = coarse_of(f, transfer);
-  int nb = div_up(f.n, TPB);
+  // full weighting: one thread per coarse cell and its far neighbours
+  // ((nc + 1)^3 owners of 2 x 2 x 2 fine points); the others one per fine point
+  int nb = transfer == SMG_TRANSFER_FW27V ? div_up((long long)(c.nx + 1) * (c.ny + 1) * (c.nz + 1), TPB)
+                                          : div_up(f.n, TPB);
   bool dbl = pk == K64;
 #define PCASE(V, BB)                                                                                   \
   if (transfer == SMG_TRANSFER_FW27V)                                                                  \
