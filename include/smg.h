@@ -96,13 +96,22 @@ enum { SMG_KRYLOV_PCG = 0, SMG_KRYLOV_FPCG = 1, SMG_KRYLOV_FGMRES = 2 };
  *  relax_w    [1.0]  Gauss-Seidel weight w of the Sec. 4.4 formulas.
  *  max_levels [16]   cap on the number of levels (>= 1).
  *  spin_budget_ms [1000] bound on any single device-side wait, in ms.
- *  use_graph  [0]    1: capture each V-cycle in a CUDA graph and replay it. */
+ *  use_graph  [0]    1: capture each V-cycle in a CUDA graph and replay it.
+ *  fuse_restrict [0] 1: the residual after pre-smoothing and its restriction
+ *                    in one kernel on scalar levels with the full-weighting
+ *                    or 3d8c restriction (fc = R (f - A u) without storing
+ *                    the fine residual); 0: two kernels.  Same arithmetic in
+ *                    the same order either way.  Off by default: the fine
+ *                    residual is FP64-bound, and the fused pass's tile-edge
+ *                    recomputation and lower occupancy cost more than the
+ *                    fine-residual traffic it saves (measured on GB300). */
 typedef struct {
   int smoother, transfer, precision, krylov, restart;
   double relax_w;
   int max_levels;
   int spin_budget_ms;
   int use_graph;
+  int fuse_restrict;
 } smg_options;
 
 /* Build the hierarchy from the finest matrix (Sec. 4.2: only the finest A is

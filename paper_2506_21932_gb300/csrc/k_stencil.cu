@@ -2,6 +2,8 @@
 // transfers (Sec. 2 V-cycle; Table 2 patterns 3d27v, 3d8c and 3d64c, and the
 // 2d4c / 2d16c pair of x-y semi-coarsening), precision
 // casts and lowering, diagonal inverses and the dense coarsest level.
+#include <algorithm>
+
 #include "ilurec.cuh"
 #include "smg_internal.cuh"
 
@@ -22,14 +24,16 @@ __device__ __forceinline__ void coords(long long p, const Grid& g, int& i, int& 
 
 // ---------------------------------------------------------------------------
 // SpMV / residual.  One thread per point, all stencil entries unrolled
-// (NS known at compile time), one fused multiply-add per coefficient.
+// (NS known at compile time), one fused multiply-add per coefficient.  With
+// skew > 0 the result goes to the point's slot in the skewed plane layout of
+// in-plane skew SB = skew (ilurec.cuh) instead of its natural index.
 // ---------------------------------------------------------------------------
 template <int PK, int NS>
 __global__ void __launch_bounds__(TPB) k_spmv1(Grid g, Stencil s, const typename Prec<PK>::val* __restrict__ A,
                                                const float* __restrict__ scale,
                                                const typename Prec<PK>::vec* __restrict__ x,
                                                const typename Prec<PK>::vec* __restrict__ b,
-                                               typename Prec<PK>::vec* __restrict__ y, int mode) {
+                                               typename Prec<PK>::vec* __restrict__ y, int mode, int skew) {
   using V = typename Prec<PK>::vec;
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= g.n) return;
@@ -43,8 +47,10 @@ __global__ void __launch_bounds__(TPB) k_spmv1(Grid g, Stencil s, const typename
     V xv = inside3(a0, a1, a2, g) ? x[p + s.lin[e]] : V(0);
     acc = fma((V)to_c(a[e]), xv, acc);
   }
-  if (PK == KBF) acc = (V)scale[p] * acc;
-  y[p] = mode ? b[p] - acc : acc;
+  // the row scale multiplies the finished sum, rounded on its own (never
+  // contracted into the subtraction below)
+  if (PK == KBF) acc = __fmul_rn(scale[p], (float)acc);
+  y[skew ? skew_slot(g, skew, i, j, k) : p] = mode ? b[p] - acc : acc;
 }
 
 // Runtime stencil size (any mask).
@@ -53,7 +59,7 @@ __global__ void __launch_bounds__(TPB) k_spmv1_any(Grid g, Stencil s, const type
                                                    const float* __restrict__ scale,
                                                    const typename Prec<PK>::vec* __restrict__ x,
                                                    const typename Prec<PK>::vec* __restrict__ b,
-                                                   typename Prec<PK>::vec* __restrict__ y, int mode) {
+                                                   typename Prec<PK>::vec* __restrict__ y, int mode, int skew) {
   using V = typename Prec<PK>::vec;
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= g.n) return;
@@ -66,8 +72,10 @@ __global__ void __launch_bounds__(TPB) k_spmv1_any(Grid g, Stencil s, const type
     V xv = inside3(a0, a1, a2, g) ? x[p + s.lin[e]] : V(0);
     acc = fma((V)to_c(a[e]), xv, acc);
   }
-  if (PK == KBF) acc = (V)scale[p] * acc;
-  y[p] = mode ? b[p] - acc : acc;
+  // the row scale multiplies the finished sum, rounded on its own (never
+  // contracted into the subtraction below)
+  if (PK == KBF) acc = __fmul_rn(scale[p], (float)acc);
+  y[skew ? skew_slot(g, skew, i, j, k) : p] = mode ? b[p] - acc : acc;
 }
 
 // 3 unknowns per point, BxB blocks (FP64 or FP32 only).
@@ -138,6 +146,99 @@ __global__ void __launch_bounds__(TPB) k_restrict_fw(Grid f, Grid c, const V* __
   }
 #pragma unroll
   for (int r = 0; r < B; ++r) fc[P * B + r] = acc[r];
+}
+
+// Residual and restriction in one pass (scalar levels): fc = R (b - A u).
+// A CTA owns a tile of kRrTJ x kRrTK coarse (j, k) columns and a chunk of
+// coarse x-planes [I0, I0 + ci).  It computes the fine residual planes its
+// coarse points read, each over the tile's fine (j, k) window, into a ring of
+// three planes in shared memory, then restricts from there.  Full weighting
+// (FW = true) reads fine planes 2I .. 2I+2 (the plane 2I+2 is kept for the
+// next coarse plane) and the window 2T+1 wide; the 3d8c sum reads 2I, 2I+1
+// and a window 2T wide, so nothing is computed twice but the one-point
+// window edge (full weighting) and the first plane of a chunk.  The residual
+// is k_spmv1's expression and the restriction k_restrict_fw's / _pc's, in
+// the same order.
+constexpr int kRrTJ = 8, kRrTK = 32;
+template <int PK, int NS, bool FW>
+__global__ void __launch_bounds__(TPB) k_resid_restrict(Grid f, Grid c, Stencil s, const typename Prec<PK>::val* __restrict__ A,
+                                                        const float* __restrict__ scale,
+                                                        const typename Prec<PK>::vec* __restrict__ x,
+                                                        const typename Prec<PK>::vec* __restrict__ b,
+                                                        typename Prec<PK>::vec* __restrict__ fc, int ci) {
+  using V = typename Prec<PK>::vec;
+  constexpr int FJ = FW ? 2 * kRrTJ + 1 : 2 * kRrTJ, FK = FW ? 2 * kRrTK + 1 : 2 * kRrTK;
+  __shared__ V rp[3][FJ * FK];
+  const int tilesK = (c.nz + kRrTK - 1) / kRrTK, tilesJ = (c.ny + kRrTJ - 1) / kRrTJ;
+  const int tile = blockIdx.x % (tilesJ * tilesK), chunk = blockIdx.x / (tilesJ * tilesK);
+  const int J0 = (tile / tilesK) * kRrTJ, K0 = (tile % tilesK) * kRrTK;
+  const int I0 = chunk * ci, I1 = min(c.nx, I0 + ci);
+  if (I0 >= I1) return;
+  // fine residual plane fx over the window into ring slot fx % 3 (zero off the grid)
+  auto plane = [&](int fx) {
+    V* dst = rp[fx % 3];
+    for (int q = threadIdx.x; q < FJ * FK; q += blockDim.x) {
+      const int fj = 2 * J0 + q / FK, fk = 2 * K0 + q % FK;
+      V r = V(0);
+      if (fx < f.nx && fj < f.ny && fk < f.nz) {
+        const long long p = ((long long)fx * f.ny + fj) * f.nz + fk;
+        const typename Prec<PK>::val* a = A + p * NS;
+        V acc = 0;
+#pragma unroll
+        for (int e = 0; e < NS; ++e) {
+          const int a0 = fx + s.off[e][0], a1 = fj + s.off[e][1], a2 = fk + s.off[e][2];
+          const V xv = inside3(a0, a1, a2, f) ? x[p + s.lin[e]] : V(0);
+          acc = fma((V)to_c(a[e]), xv, acc);
+        }
+        if (PK == KBF) acc = __fmul_rn(scale[p], (float)acc);  // rounded on its own, as in k_spmv1
+        r = b[p] - acc;
+      }
+      dst[q] = r;
+    }
+  };
+  if (FW) plane(2 * I0);
+  for (int I = I0; I < I1; ++I) {
+    if (FW) {
+      plane(2 * I + 1);
+      plane(2 * I + 2);
+    } else {
+      plane(2 * I);
+      plane(2 * I + 1);
+    }
+    __syncthreads();
+    const int jj = threadIdx.x / kRrTK, kk = threadIdx.x % kRrTK;
+    const int J = J0 + jj, K = K0 + kk;
+    if (threadIdx.x < kRrTJ * kRrTK && J < c.ny && K < c.nz) {
+      V acc = 0;
+      if (FW) {
+        const V w1[3] = {V(0.5), V(1), V(0.5)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (2 * I + a >= f.nx) continue;
+          const V* pl = rp[(2 * I + a) % 3];
+#pragma unroll
+          for (int bb = 0; bb < 3; ++bb) {
+            if (2 * J + bb >= f.ny) continue;
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+              if (2 * K + cc >= f.nz) continue;
+              const V wgt = w1[a] * w1[bb] * w1[cc] * V(0.125);
+              acc = fma(wgt, pl[(2 * jj + bb) * FK + 2 * kk + cc], acc);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) acc += rp[(2 * I + a) % 3][(2 * jj + bb) * FK + 2 * kk + cc];
+      }
+      fc[((long long)I * c.ny + J) * c.nz + K] = acc;
+    }
+    __syncthreads();
+  }
 }
 
 template <typename V, int B>
@@ -691,9 +792,11 @@ __global__ void k_dense_matvec(int n, const double* __restrict__ Minv, const dou
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_spmv(const LevelView& L, const void* x, const void* b, void* y, int mode, cudaStream_t st) {
+cudaError_t launch_spmv(const LevelView& L, const void* x, const void* b, void* y, int mode, cudaStream_t st,
+                        int skew) {
   int nb = div_up(L.g.n, TPB);
   if (L.B == 3) {
+    if (skew) return cudaErrorInvalidValue;  // block levels have no skewed layout
     if (L.pk == K64)
       k_spmv3<double><<<nb, TPB, 0, st>>>(L.g, L.s, (const double*)L.A, (const double*)x, (const double*)b,
                                           (double*)y, mode);
@@ -708,13 +811,13 @@ cudaError_t launch_spmv(const LevelView& L, const void* x, const void* b, void* 
     using Vec = typename Prec<PK>::vec;                                                                        \
     if (L.s.ns == 27)                                                                                          \
       k_spmv1<PK, 27><<<nb, TPB, 0, st>>>(L.g, L.s, (const Val*)L.A, L.scale, (const Vec*)x, (const Vec*)b,    \
-                                          (Vec*)y, mode);                                                      \
+                                          (Vec*)y, mode, skew);                                                      \
     else if (L.s.ns == 7)                                                                                      \
       k_spmv1<PK, 7><<<nb, TPB, 0, st>>>(L.g, L.s, (const Val*)L.A, L.scale, (const Vec*)x, (const Vec*)b,     \
-                                         (Vec*)y, mode);                                                       \
+                                         (Vec*)y, mode, skew);                                                       \
     else                                                                                                       \
       k_spmv1_any<PK><<<nb, TPB, 0, st>>>(L.g, L.s, (const Val*)L.A, L.scale, (const Vec*)x, (const Vec*)b,    \
-                                          (Vec*)y, mode);                                                      \
+                                          (Vec*)y, mode, skew);                                                      \
   }
   if (L.pk == K64) SPMV_CASE(K64)
   else if (L.pk == K32) SPMV_CASE(K32)
@@ -747,6 +850,48 @@ cudaError_t launch_restrict(int transfer, Grid f, int B, int pk, const void* rf,
     if (B == 1) { RCASE(float, 1) } else { RCASE(float, 3) }
   }
 #undef RCASE
+  smg_count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid_restrict(const LevelView& L, int transfer, const void* x, const void* b, void* fc,
+                                  cudaStream_t st) {
+  const bool fw = transfer == SMG_TRANSFER_FW27V;
+  if (L.B != 1 || !(fw || transfer == SMG_TRANSFER_PC8C || transfer == SMG_TRANSFER_C64C) ||
+      !(L.s.ns == 7 || L.s.ns == 19 || L.s.ns == 27))
+    return cudaErrorNotSupported;
+  const Grid c = coarse_of(L.g, transfer);
+  if (!fw && (L.g.nx != 2 * c.nx || L.g.ny != 2 * c.ny || L.g.nz != 2 * c.nz)) return cudaErrorNotSupported;
+  const long long tiles = (long long)((c.ny + kRrTJ - 1) / kRrTJ) * ((c.nz + kRrTK - 1) / kRrTK);
+  // enough CTAs for two per SM: split the coarse x-planes into chunks
+  int dev = 0, nsm = 0;
+  cudaError_t ae = cudaGetDevice(&dev);
+  if (ae == cudaSuccess) ae = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (ae != cudaSuccess) return ae;
+  const long long want = (2LL * nsm + tiles - 1) / tiles;
+  const int chunks = (int)std::max(1LL, std::min((long long)c.nx, want));
+  const int ci = (c.nx + chunks - 1) / chunks;
+  const int nb = (int)(tiles * ((c.nx + ci - 1) / ci));
+#define RR_CASE(PK, NSV)                                                                                      \
+  {                                                                                                           \
+    using Val = typename Prec<PK>::val;                                                                       \
+    using Vec = typename Prec<PK>::vec;                                                                       \
+    if (fw)                                                                                                   \
+      k_resid_restrict<PK, NSV, true><<<nb, TPB, 0, st>>>(L.g, c, L.s, (const Val*)L.A, L.scale, (const Vec*)x,  \
+                                                         (const Vec*)b, (Vec*)fc, ci);                        \
+    else                                                                                                      \
+      k_resid_restrict<PK, NSV, false><<<nb, TPB, 0, st>>>(L.g, c, L.s, (const Val*)L.A, L.scale, (const Vec*)x, \
+                                                          (const Vec*)b, (Vec*)fc, ci);                       \
+  }
+#define RR_NS(PK)                           \
+  if (L.s.ns == 27) RR_CASE(PK, 27)         \
+  else if (L.s.ns == 19) RR_CASE(PK, 19)    \
+  else RR_CASE(PK, 7)
+  if (L.pk == K64) { RR_NS(K64) }
+  else if (L.pk == K32) { RR_NS(K32) }
+  else { RR_NS(KBF) }
+#undef RR_NS
+#undef RR_CASE
   smg_count_launch(1);
   return cudaGetLastError();
 }

@@ -301,12 +301,11 @@ static int smooth_pre(smg_ctx* h, Level& L, int l, const void* f, void* u, cudaS
 static int smooth_post(smg_ctx* h, Level& L, int l, const void* f, void* u, cudaStream_t st) {
   if (skewed(L)) {
     if (h->opt.smoother == SMG_SMOOTHER_ILU0) {
-      // u += U^-1 L^-1 (f - A u): the residual in natural order, the solves
-      // on skewed vectors, the correction added while unpacking
-      SMG_CUDA_TRY(launch_spmv(view(h, L, true), u, f, L.t, 1, st));
+      // u += U^-1 L^-1 (f - A u): the residual computed in natural order
+      // and written in the skewed layout, the solves on skewed vectors, the
+      // correction added while unpacking
+      SMG_CUDA_TRY(launch_spmv(view(h, L, true), u, f, L.vs0, 1, st, L.cfg.SB));
       prof_mark(h, l, PM_POST_RESID, st);
-      TRY(skew(h, L, L.t, L.vs0, true, false, st));
-      prof_mark(h, l, PM_PACK, st);
       TRY(sweep_rec(h, L, SW_ILU_L, +1, L.vs0, L.vs1, st));
       prof_mark(h, l, PM_POST1, st);
       TRY(sweep_rec(h, L, SW_ILU_U, -1, L.vs1, L.vs1, st));
@@ -406,9 +405,19 @@ static int vcycle_body(smg_ctx* h, const double* r, double* z, cudaStream_t st) 
   for (int l = 0; l < nl - 1; ++l) {
     Level& L = h->L[l];
     TRY(smooth_pre(h, L, l, F(l), U(l), st));
-    SMG_CUDA_TRY(launch_spmv(view(h, L, true), U(l), F(l), L.t, 1, st));
-    prof_mark(h, l, PM_RESID, st);
-    SMG_CUDA_TRY(launch_restrict(h->opt.transfer, L.g, h->B, h->pk, L.t, h->L[l + 1].f, st));
+    // f_{l+1} = R (f - A u): one fused pass where the level allows it
+    const cudaError_t rr = h->opt.fuse_restrict
+                               ? launch_resid_restrict(view(h, L, true), h->opt.transfer, U(l), F(l), h->L[l + 1].f, st)
+                               : cudaErrorNotSupported;
+    if (rr == cudaSuccess) {
+      prof_mark(h, l, PM_RESID, st);
+    } else if (rr == cudaErrorNotSupported) {
+      SMG_CUDA_TRY(launch_spmv(view(h, L, true), U(l), F(l), L.t, 1, st));
+      prof_mark(h, l, PM_RESID, st);
+      SMG_CUDA_TRY(launch_restrict(h->opt.transfer, L.g, h->B, h->pk, L.t, h->L[l + 1].f, st));
+    } else {
+      SMG_CUDA_TRY(rr);
+    }
     prof_mark(h, l, PM_RESTRICT, st);
   }
   TRY(coarse_solve(h, F(nl - 1), U(nl - 1), st));
@@ -798,6 +807,7 @@ extern "C" int smg_setup(smg_t* out, const int dims[3], int nstencil, const int*
   if (!(o.relax_w > 0.0 && o.relax_w < 2.0)) return SMG_EINVAL;
   if (o.max_levels < 0) return SMG_EINVAL;
   if (o.spin_budget_ms <= 0) o.spin_budget_ms = 1000;
+  if (o.fuse_restrict < 0 || o.fuse_restrict > 1) return SMG_EINVAL;
   if (block == 3 && (o.smoother != SMG_SMOOTHER_SGS || o.precision == SMG_PREC_BF16)) return SMG_EINVAL;
   if (o.smoother == SMG_SMOOTHER_ILU0 && nstencil != 7 && nstencil != 19 && nstencil != 27) return SMG_EINVAL;
   // line Gauss-Seidel: scalar FP64 hierarchy, weight 1, columns of at most 1024 points

@@ -148,7 +148,15 @@ struct LevelView {
 };
 
 // y = A x (mode 0) or y = b - A x (mode 1).
-cudaError_t launch_spmv(const LevelView& L, const void* x, const void* b, void* y, int mode, cudaStream_t st);
+// fc = R (b - A x) in one pass for scalar levels and the full-weighting or
+// 3d8c restriction; cudaErrorNotSupported otherwise (the caller then runs
+// launch_spmv and launch_restrict)
+cudaError_t launch_resid_restrict(const LevelView& L, int transfer, const void* x, const void* b, void* fc,
+                                  cudaStream_t st);
+// y = A x (mode 0) or b - A x (mode 1); skew > 0 writes y in the skewed
+// plane layout of in-plane skew skew (scalar levels only)
+cudaError_t launch_spmv(const LevelView& L, const void* x, const void* b, void* y, int mode, cudaStream_t st,
+                        int skew = 0);
 
 // Restriction / prolongation between level (g, B) and its coarse level.
 cudaError_t launch_restrict(int transfer, Grid fine, int B, int pk, const void* rf, void* fc, cudaStream_t st);

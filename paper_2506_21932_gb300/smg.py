@@ -33,7 +33,8 @@ class SmgError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("transfer", ctypes.c_int), ("precision", ctypes.c_int),
                 ("krylov", ctypes.c_int), ("restart", ctypes.c_int), ("relax_w", ctypes.c_double),
-                ("max_levels", ctypes.c_int), ("spin_budget_ms", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("max_levels", ctypes.c_int), ("spin_budget_ms", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("fuse_restrict", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -194,7 +195,8 @@ class SMG:
     """A structured-multigrid hierarchy living on the current CUDA device."""
 
     def __init__(self, dims, offsets, coeffs, block=1, smoother=SGS, transfer=FW27V, precision=FP64,
-                 krylov=PCG, restart=30, relax_w=1.0, max_levels=0, spin_budget_ms=0, use_graph=0, stream=None):
+                 krylov=PCG, restart=30, relax_w=1.0, max_levels=0, spin_budget_ms=0, use_graph=0, fuse_restrict=0,
+                 stream=None):
         import torch
         if not (coeffs.is_cuda and coeffs.dtype == torch.float64 and coeffs.is_contiguous()):
             raise ValueError("coeffs must be a contiguous float64 CUDA tensor")
@@ -203,7 +205,8 @@ class SMG:
         self.block = int(block)
         self.n = self.dims[0] * self.dims[1] * self.dims[2]
         self.precision = precision
-        opt = Options(smoother, transfer, precision, krylov, restart, relax_w, max_levels, spin_budget_ms, use_graph)
+        opt = Options(smoother, transfer, precision, krylov, restart, relax_w, max_levels, spin_budget_ms, use_graph,
+                      fuse_restrict)
         offs = [c for o in offsets for c in o]
         h = ctypes.c_void_p()
         rc = self._lib.smg_setup(ctypes.byref(h), _iarr(self.dims), len(offsets), _iarr(offs),

@@ -274,6 +274,30 @@ def test_vcycle(S, orc, d, kind, smoother, transfer, B):
     assert rel2(host(z), ref.vcycle(r)) < TOL_VCYCLE
 
 
+@pytest.mark.parametrize("d,kind,smoother,transfer,prec", [
+    ((16, 20, 72), "q1", "ilu", "fw", 0), ((16, 20, 72), "lap", "sgs", "fw", 0), ((12, 36, 40), "q1", "ilu", "fw", 1),
+    ((16, 20, 72), "q1", "ilu", "fw", 2), ((16, 20, 72), "fv", "ilu", "c64", 0), ((16, 20, 72), "lap", "sgs", "pc", 1),
+])
+def test_fused_residual_restriction_equals_two_kernels(S, d, kind, smoother, transfer, prec):
+    """One pass for f_c = R (f - A u) (option fuse_restrict) gives the same
+    V-cycle, bit for bit, as the residual and restriction kernels: the same
+    expressions in the same order.  The sizes leave ragged coarse tiles in j
+    and k and several x-chunks."""
+    off, A = problem(kind, d)
+    sm = {"ilu": S.ILU0, "sgs": S.SGS}[smoother]
+    tr = {"fw": S.FW27V, "c64": S.C64C, "pc": S.PC8C}[transfer]
+    kry = S.PCG if prec == 0 else S.FPCG
+    r = cu(I.rhs(np.prod(d), 5).numpy())
+    z = []
+    for fuse in (0, 1):
+        h = make(S, d, off, A, smoother=sm, transfer=tr, precision=prec, krylov=kry, fuse_restrict=fuse)
+        zz = torch.empty_like(r)
+        h.vcycle(r, zz)
+        h.close()
+        z.append(zz)
+    assert torch.equal(z[0], z[1])
+
+
 def test_vcycle_graph_replay_is_bitwise_identical(S):
     d = (32, 32, 32)
     off, A = problem("q1", d)
@@ -529,6 +553,11 @@ def test_launch_counter_counts_kernels(S):
     # prolongation; plus the coarsest solve
     nl = h.nlevels
     assert per == 12 * (nl - 1) + 1
+    # residual and restriction in one kernel
+    hf = make(S, d, off, A, fuse_restrict=1)
+    c0 = S.launch_count()
+    hf.vcycle(r, z)
+    assert S.launch_count() - c0 == 11 * (nl - 1) + 1
     hg = make(S, d, off, A, use_graph=1)
     c0 = S.launch_count()
     hg.vcycle(r, z)
