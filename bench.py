@@ -96,8 +96,8 @@ FP64_PROBE = os.path.join(ROOT, "profiles", "fp64_fma_peak_gb300.txt")
 # by (smoother, stencil points, precision).  Absent where no capture of the
 # current kernel exists.
 TRAFFIC_PER_POINT = {
-    # k_sweep3 ILU lower solve, FP64, 27 points: 267.9 MB for 128^3
-    (1, 27, 0): (267.864e6 / 128 ** 3, "profiles/k_sweep3_ilu_lower_aniso27_128cubed.md"),
+    # k_sweep3 ILU lower solve, FP64, 27 points: 268.97 MB for 128^3
+    (1, 27, 0): (268.970e6 / 128 ** 3, "profiles/k_sweep3_ilu_lower_aniso27_128cubed.md"),
 }
 
 
