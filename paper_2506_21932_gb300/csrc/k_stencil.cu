@@ -768,6 +768,168 @@ __global__ void k_gj_elim(int n, int col, double* M, double* Minv, const double*
   }
 }
 
+// The same Gauss-Jordan elimination in one persistent launch (every CTA
+// resident: cooperative launch).  Per column k two grid barriers:
+//  (1) every CTA reduces the partial pivot candidates of all CTAs (largest
+//      |M[r][k]| over r >= k, the smallest row among equal values: the choice
+//      of k_gj_pivot), then swaps rows k and p and scales the new row k by
+//      1 / pivot, columns spread over the whole grid;
+//  (2) CTA b eliminates column k from its rows r = b, b + G, ... (the same
+//      update, expression and skips as k_gj_elim) and leaves the partial
+//      pivot candidate of column k + 1 among them.
+// The barrier is a counter and a generation word in global memory, waited
+// on with a bound; a timeout or a zero pivot ends every CTA at the next
+// barrier with the error word set.
+struct GjGrid {
+  int n;
+  double* M;
+  double* Minv;
+  double* part;   // [3 * gridDim.x]: candidate |value|, row and signed value of each CTA
+  unsigned* bar;  // [2]: arrivals, generation (zero before the launch)
+  int* err;
+  unsigned long long budget_ns;
+};
+
+__device__ bool gj_grid_sync(const GjGrid& A, unsigned& gen) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    if (atomicAdd(&A.bar[0], 1u) == gridDim.x - 1) {
+      atomicExch(&A.bar[0], 0u);
+      __threadfence();
+      atomicExch(&A.bar[1], gen + 1);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      for (;;) {
+        unsigned g;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(A.bar + 1) : "memory");
+        if (g != gen) break;
+        if (globaltimer_ns() - t0 > A.budget_ns) {
+          atomicCAS(A.err, 0, DEV_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok && ld_relaxed(A.err) == 0;
+  }
+  __syncthreads();
+  ++gen;
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(TPB) k_gj_persistent(GjGrid A) {
+  __shared__ double sv[TPB], sw[TPB];
+  __shared__ int si[TPB];
+  const int n = A.n, G = gridDim.x, t = threadIdx.x;
+  double* M = A.M;
+  double* Minv = A.Minv;
+  unsigned gen = 0;
+  const long long gtid = (long long)blockIdx.x * TPB + t, gstride = (long long)G * TPB;
+  for (long long idx = gtid; idx < (long long)n * n; idx += gstride) Minv[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+  // partial pivot candidate of column k among this CTA's rows r >= k
+  auto candidate = [&](int k) {
+    double best = -1.0, bv = 0.0;
+    int bi = n;
+    for (int r = blockIdx.x + G * t; r < n; r += G * TPB)
+      if (r >= k) {
+        const double x = M[(long long)r * n + k], v = fabs(x);
+        if (v > best) { best = v; bi = r; bv = x; }
+      }
+    sv[t] = best;
+    si[t] = bi;
+    sw[t] = bv;
+    __syncthreads();
+    for (int h = TPB / 2; h > 0; h >>= 1) {
+      if (t < h && (sv[t + h] > sv[t] || (sv[t + h] == sv[t] && si[t + h] < si[t]))) {
+        sv[t] = sv[t + h];
+        si[t] = si[t + h];
+        sw[t] = sw[t + h];
+      }
+      __syncthreads();
+    }
+    if (t == 0) {
+      A.part[3 * blockIdx.x] = sv[0];
+      A.part[3 * blockIdx.x + 1] = (double)si[0];
+      A.part[3 * blockIdx.x + 2] = sw[0];
+    }
+  };
+  candidate(0);
+  for (int k = 0; k < n; ++k) {
+    if (!gj_grid_sync(A, gen)) return;
+    // (1) the pivot, from every CTA's candidate (the same answer in every CTA)
+    double best = -1.0, pvs = 0.0;
+    int p = n;
+    for (int q = t; q < G; q += TPB) {
+      const double v = A.part[3 * q];
+      const int r = (int)A.part[3 * q + 1];
+      if (v > best || (v == best && r < p)) { best = v; p = r; pvs = A.part[3 * q + 2]; }
+    }
+    sv[t] = best;
+    si[t] = p;
+    sw[t] = pvs;
+    __syncthreads();
+    for (int h = TPB / 2; h > 0; h >>= 1) {
+      if (t < h && (sv[t + h] > sv[t] || (sv[t + h] == sv[t] && si[t + h] < si[t]))) {
+        sv[t] = sv[t + h];
+        si[t] = si[t + h];
+        sw[t] = sw[t + h];
+      }
+      __syncthreads();
+    }
+    best = sv[0];
+    p = si[0];
+    pvs = sw[0];  // the pivot M[p][k] itself (its row is rewritten below)
+    __syncthreads();
+    if (!(best > 0.0)) {
+      if (blockIdx.x == 0 && t == 0) atomicCAS(A.err, 0, SMG_EBREAKDOWN);
+      return;
+    }
+    const double inv = 1.0 / pvs;
+    for (long long c = gtid; c < n; c += gstride) {
+      const double mk = M[(long long)k * n + c], mp = M[(long long)p * n + c];
+      const double ik = Minv[(long long)k * n + c], ip = Minv[(long long)p * n + c];
+      M[(long long)k * n + c] = mp * inv;
+      Minv[(long long)k * n + c] = ip * inv;
+      if (p != k) {
+        M[(long long)p * n + c] = mk;
+        Minv[(long long)p * n + c] = ik;
+      }
+    }
+    if (!gj_grid_sync(A, gen)) return;
+    // (2) eliminate column k from this CTA's rows
+    const double* rk = M + (long long)k * n;
+    const double* ik = Minv + (long long)k * n;
+    for (int r = blockIdx.x; r < n; r += G) {
+      if (r == k) continue;
+      double* rr = M + (long long)r * n;
+      const double f = rr[k];
+      if (f == 0.0) continue;
+      double* ir = Minv + (long long)r * n;
+      __syncthreads();  // every thread has read rr[k] before it is cleared
+      for (int c = t; c < n; c += TPB) {
+        if (c == k) {
+          rr[c] = 0.0;
+          continue;
+        }
+        const double pv = rk[c];
+        if (pv == 0.0) continue;
+        rr[c] -= f * pv;
+      }
+      for (int c = t; c < n; c += TPB) {
+        const double pv = ik[c];
+        if (pv == 0.0) continue;
+        ir[c] -= f * pv;
+      }
+    }
+    __syncthreads();
+    if (k + 1 < n) candidate(k + 1);
+  }
+}
+
 __global__ void k_set_identity(int n, double* Minv) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n * n) return;
@@ -1025,7 +1187,30 @@ cudaError_t launch_assemble_dense(Grid g, const Stencil& s, int B, const double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_gauss_jordan(int n, double* M, double* Minv, double* colbuf, int* err, cudaStream_t st) {
+cudaError_t launch_gauss_jordan(int n, double* M, double* Minv, double* colbuf, int* err, cudaStream_t st,
+                                double* scratch, unsigned long long budget_ns) {
+  if (scratch) {
+    // one persistent cooperative launch (every CTA resident), at most
+    // kGjMaxBlocks CTAs; the per-column launches below when it cannot run
+    int dev = 0, nsm = 0, per = 0, coop = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gj_persistent, TPB, 0);
+    if (e != cudaSuccess) return e;
+    if (coop && per > 0) {
+      GjGrid A{n, M, Minv, scratch, (unsigned*)(scratch + 3 * kGjMaxBlocks), err, budget_ns};
+      e = cudaMemsetAsync(A.bar, 0, 2 * sizeof(unsigned), st);
+      if (e != cudaSuccess) return e;
+      const int grid = std::min(nsm * per, kGjMaxBlocks);
+      void* args[] = {&A};
+      e = cudaLaunchCooperativeKernel((const void*)k_gj_persistent, grid, TPB, args, 0, st);
+      smg_count_launch(1);
+      if (e == cudaSuccess) return cudaSuccess;
+      if (e != cudaErrorCooperativeLaunchTooLarge) return e;
+      (void)cudaGetLastError();
+    }
+  }
   k_set_identity<<<div_up((long long)n * n, TPB), TPB, 0, st>>>(n, Minv);
   int nb = div_up((long long)n * 2 * n, TPB);
   for (int col = 0; col < n; ++col) {

@@ -749,14 +749,16 @@ static int do_setup(smg_ctx* h, const int dims[3], int ns, const int* offsets, c
     Level& Lc = h->L[h->nlev - 1];
     h->nco = (int)(Lc.g.n * B);
     if (h->nco > 8192) return SMG_EINVAL;
-    double *M, *colbuf;
+    double *M, *colbuf, *gjs;
     TRY(dalloc(h, &M, (size_t)h->nco * h->nco));
     TRY(dalloc(h, &h->cinv, (size_t)h->nco * h->nco));
     TRY(dalloc(h, &colbuf, h->nco));
+    TRY(dalloc(h, &gjs, kGjScratchDoubles));
     TRY(dalloc(h, &h->cf, h->nco));
     TRY(dalloc(h, &h->cu, h->nco));
     SMG_CUDA_TRY(launch_assemble_dense(Lc.g, Lc.s, B, Lc.A, M, st));
-    SMG_CUDA_TRY(launch_gauss_jordan(h->nco, M, h->cinv, colbuf, h->err, st));
+    SMG_CUDA_TRY(launch_gauss_jordan(h->nco, M, h->cinv, colbuf, h->err, st, gjs,
+                                     (unsigned long long)h->opt.spin_budget_ms * 1000000ull));
   }
   // Krylov storage
   const long long n0 = h->L[0].g.n * B;

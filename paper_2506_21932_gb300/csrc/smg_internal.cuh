@@ -257,7 +257,14 @@ cudaError_t launch_d2f_array(const double* a, float* b, long long n, cudaStream_
 // Dense coarsest level: assemble, Gauss-Jordan inverse with partial pivoting,
 // apply (y = Minv x, double).
 cudaError_t launch_assemble_dense(Grid g, const Stencil& s, int B, const double* A, double* M, cudaStream_t st);
-cudaError_t launch_gauss_jordan(int n, double* M, double* Minv, double* colbuf, int* err, cudaStream_t st);
+// Dense inverse Minv = M^-1 (M destroyed) by Gauss-Jordan elimination with
+// partial pivoting.  With scratch (kGjScratchDoubles doubles) one persistent
+// cooperative launch whose grid barriers wait at most budget_ns; otherwise
+// (or when the device cannot co-schedule the grid) two launches per column.
+constexpr int kGjMaxBlocks = 1024;
+constexpr int kGjScratchDoubles = 3 * kGjMaxBlocks + 2;
+cudaError_t launch_gauss_jordan(int n, double* M, double* Minv, double* colbuf, int* err, cudaStream_t st,
+                                double* scratch = nullptr, unsigned long long budget_ns = 0);
 cudaError_t launch_dense_matvec(int n, const double* Minv, const double* x, double* y, cudaStream_t st);
 
 // Deterministic reduction workspace of the Krylov kernels: per-block

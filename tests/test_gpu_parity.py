@@ -188,6 +188,23 @@ def test_ilu0_tridiagonal_exact_solve(S, orc):
     assert rel_max(orc.spmv(d, I.OFF7, A, host(y)), b) < 1e-12
 
 
+def test_coarsest_inverse_with_row_exchanges(S, orc):
+    """The dense coarsest inverse (Gauss-Jordan, partial pivoting) of a
+    1440-unknown level whose centre coefficients are shrunk a thousandfold,
+    so that most columns need a row exchange: the direct solve agrees with a
+    dense LU solve of the assembled matrix."""
+    d = (6, 10, 24)
+    A = rnd_sym27(d, 7)
+    A[:, I.OFF27.index((0, 0, 0))] *= 1e-3
+    h = make(S, d, I.OFF27, A, smoother=S.SGS, max_levels=1)
+    assert h.nlevels == 1
+    b = np.random.default_rng(2).normal(size=A.shape[0])
+    y = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+    h.level_apply(0, S.OP_COARSE_SOLVE, b=cu(b), y=y)
+    x_ref = np.linalg.solve(orc.assemble_dense(d, I.OFF27, A), b)
+    assert rel2(host(y), x_ref) < 1e-9
+
+
 # ---------------------------------------------------------------------------
 # hierarchy: Galerkin coarse operators, transfers
 # ---------------------------------------------------------------------------
