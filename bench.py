@@ -457,18 +457,26 @@ def run_ours(args, w, rank, world):
     lk_h = None if logk is None else logk.cpu().pin_memory()
     lk_d = None if logk is None else torch.empty_like(logk)
 
+    phase = []  # per step: (start, copies in, solved, copied out) events
+
     def e2e_step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(st)
         A_d.copy_(A_h, non_blocking=True)
         b_d.copy_(b_h, non_blocking=True)
         if lk_d is not None:
             lk_d.copy_(lk_h, non_blocking=True)
+        ev[1].record(st)
         hh = make_ctx(main_prec, A_d, lk_d)
         x_d.zero_()
         it, rr, rc = hh.solve(b_d, x_d, tol=w["tol"], maxit=1000, check=False)
         hh.close()
         if rc != 0:
             raise RuntimeError("e2e solve failed: status %d" % rc)
+        ev[2].record(st)
         x_h.copy_(x_d, non_blocking=True)
+        ev[3].record(st)
+        phase.append(ev)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -482,8 +490,15 @@ def run_ours(args, w, rank, world):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / ne
     e2e_wall = (time.perf_counter() - t0) / ne * 1e3
-    out.update(e2e_ms=max_over_ranks(max(e2e_ms, e2e_wall), dev, world),
-               h2d=A.numel() * 8 + n * 8 + (0 if logk is None else logk.numel() * 8), d2h=n * 8)
+    h2d = A.numel() * 8 + n * 8 + (0 if logk is None else logk.numel() * 8)
+    timed = phase[-ne:]
+    cin = sum(ev[0].elapsed_time(ev[1]) for ev in timed) / ne
+    comp = sum(ev[1].elapsed_time(ev[2]) for ev in timed) / ne
+    cout = sum(ev[2].elapsed_time(ev[3]) for ev in timed) / ne
+    out.update(e2e_ms=max_over_ranks(max(e2e_ms, e2e_wall), dev, world), h2d=h2d, d2h=n * 8,
+               e2e_phases={"h2d_ms": round(cin, 3), "h2d_gbs": round(h2d / (cin * 1e-3) / 1e9, 1),
+                           "setup_and_solve_ms": round(comp, 3), "d2h_ms": round(cout, 3),
+                           "wall_ms": round(e2e_wall, 3), "events_ms": round(e2e_ms, 3)})
     return out
 
 
@@ -607,8 +622,8 @@ def main():
             "vcycle_ms": vc["vcycle_ms"], "vcycle_gbs": vc["vcycle_gbs"], "vcycle_hbm_frac": vc["vcycle_hbm_frac"],
             "roofline": r["roof"],
             "cpu_baseline": cpu,
-            "e2e": {"value": round(r["e2e_ms"] / 1e3, 5), "unit": "s", "h2d_bytes_per_step": int(r["h2d"]),
-                    "d2h_bytes_per_step": int(r["d2h"])},
+            "e2e": dict({"value": round(r["e2e_ms"] / 1e3, 5), "unit": "s", "h2d_bytes_per_step": int(r["h2d"]),
+                         "d2h_bytes_per_step": int(r["d2h"])}, **({"phases": r["e2e_phases"]} if "e2e_phases" in r else {})),
             "gpu_launches": int(r["launches"]), "clocks": r["clocks"]}
     line.update(r.get("extra", {}))
     print(json.dumps(line), flush=True)
