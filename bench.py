@@ -65,6 +65,12 @@ WORKLOADS = {
                                                                           batch=4, lr=1e-3)),
     "c5_plain": dict(desc="varcoef7_256^3_sgs_fw27v_pcg_fp64", dims=(256, 256, 256), gen="fv", smoother=0,
                      transfer=0, precision=0, krylov=0, tol=1e-9),
+    # the network in place of the finest level's post-smoothing (trained on the
+    # residuals the coarse correction leaves; rejected corrections fall back
+    # to the skipped post-smoothing)
+    "c5_replace": dict(desc="varcoef7_256^3_sgs_fw27v_fpcg_cnn_replaces_post_fp64", dims=(256, 256, 256), gen="fv",
+                       smoother=0, transfer=0, precision=0, krylov=1, tol=1e-9,
+                       learned=dict(dims=(64, 64, 64), fields=20, pairs=2000, batch=4, lr=1e-3, mode=1)),
     # the same cell-centred variable-coefficient 7-point matrix with ILU(0) and
     # the cell-centred transfer pair (3d64c interpolation, 3d8c restriction:
     # Table 8's rhd-3T setting), whose V-cycle is nonsymmetric -> FPCG / FGMRES;
@@ -143,6 +149,7 @@ def train_post_smoother(w, dev):
     for f in range(cfg["fields"]):
         off, A, _, logk = make_problem(tw, 1000 + f, dev, with_logk=True)
         mgs.append(smg.SMG(cfg["dims"], off, A, smoother=w["smoother"], transfer=w["transfer"], krylov=1))
+        mgs[-1].set_learned_mode(cfg.get("mode", 0))
         lks.append(logk)
     tr = PostSmootherTrainer(mgs, lks, seed=0, lr=cfg["lr"], batch=cfg["batch"])
     loss0 = tr.eval_loss(8)
@@ -267,6 +274,7 @@ def run_ours(args, w, rank, world):
     def make_ctx(prec, Amat, lk=logk):
         h = smg.SMG(w["dims"], off, Amat, **opts(prec))
         if theta is not None and prec == main_prec:
+            h.set_learned_mode(w["learned"].get("mode", 0))
             h.set_learned_smoother(theta, lk)
         return h
 

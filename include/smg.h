@@ -322,6 +322,17 @@ int smg_cnn_adam(int n, float* theta, float* m, float* v, const float* grad, int
  * The preconditioner is then nonlinear: the context's Krylov method must be
  * FPCG or FGMRES (SMG_EINVAL otherwise); one unknown per point only. */
 int smg_set_learned_smoother(smg_t h, const float* theta, const double* logk, void* stream);
+/* Where the attached network acts (not in the paper).  SMG_LEARNED_AFTER
+ * (default): after the whole V-cycle, as above.  SMG_LEARNED_REPLACE: in
+ * place of the finest level's post-smoothing: the V-cycle skips that
+ * smoothing (also in smg_learned_sample, so the training pairs are the
+ * residuals the coarse correction leaves), the correction is tested the same
+ * way, and when it is rejected the skipped post-smoothing runs, so the
+ * result is then exactly the plain V-cycle's (the decision is read back to
+ * the host: one synchronisation per V-cycle).  FP64 hierarchies only.
+ * Errors: SMG_EINVAL (NULL handle, bad mode, reduced-precision hierarchy). */
+enum { SMG_LEARNED_AFTER = 0, SMG_LEARNED_REPLACE = 1 };
+int smg_set_learned_mode(smg_t h, int mode);
 /* One training pair for the post-smoother, built on the device from a known
  * error e0 (double [n], device): r0 = A e0, z = V-cycle(r0) (the plain one,
  * even when a network is attached), e1 = e0 - z (the exact error the V-cycle

@@ -106,6 +106,11 @@ struct smg_ctx {
   int kernels_per_vcycle = 0;
   // learned post-smoother of the finest level (null when detached)
   const double* ls_logk = nullptr;
+  // SMG_LEARNED_REPLACE: the network stands in for the finest level's
+  // post-smoothing (which the V-cycle then skips while a network is attached
+  // and while training pairs are drawn)
+  int ls_mode = 0;
+  bool ls_sampling = false;
   void* ls_ws = nullptr;
   CnnWork ls_w{};
   double *ls_r = nullptr, *ls_d = nullptr, *ls_t = nullptr;
@@ -379,6 +384,16 @@ static int learned_post_smooth(smg_ctx* h, const double* r, double* z, cudaStrea
   SMG_CUDA_TRY(launch_spmv(A0, h->ls_d, h->ls_r, h->ls_t, 1, st));
   SMG_CUDA_TRY(kry_dot(n, h->ls_t, h->ls_t, h->sc, SC_LS_WW, h->rw, st));
   SMG_CUDA_TRY(cnn_post_glue(2, n, nullptr, z, h->ls_d, h->sc + SC_LS_WW, h->sc + SC_LS_RR, nullptr, nullptr, st));
+  if (h->ls_mode == SMG_LEARNED_REPLACE) {
+    // the correction stood in for the post-smoothing: when the test above
+    // rejected it (z unchanged), run the skipped post-smoothing, so z is the
+    // plain V-cycle's result
+    double nrm[2];
+    SMG_CUDA_TRY(cudaMemcpyAsync(&nrm[0], h->sc + SC_LS_WW, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SMG_CUDA_TRY(cudaMemcpyAsync(&nrm[1], h->sc + SC_LS_RR, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SMG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!(nrm[0] < nrm[1])) TRY(smooth_post(h, h->L[0], 0, r, z, st));
+  }
   return SMG_OK;
 }
 
@@ -426,7 +441,8 @@ static int vcycle_body(smg_ctx* h, const double* r, double* z, cudaStream_t st) 
     Level& L = h->L[l];
     SMG_CUDA_TRY(launch_prolong_add(h->opt.transfer, L.g, h->B, h->pk, h->L[l + 1].u, U(l), st));
     prof_mark(h, l, PM_PROLONG, st);
-    TRY(smooth_post(h, L, l, F(l), U(l), st));
+    const bool replaced = l == 0 && h->ls_mode == SMG_LEARNED_REPLACE && (h->ls_logk || h->ls_sampling);
+    if (!replaced) TRY(smooth_post(h, L, l, F(l), U(l), st));
   }
   if (h->pk != K64) {
     SMG_CUDA_TRY(launch_cast_f2d((const float*)u0, z, n0, st));
@@ -1197,8 +1213,10 @@ extern "C" int smg_learned_sample(smg_t h, const double* e0, const double* logk,
   const LevelView A0 = view(h, L0, false);
   SMG_CUDA_TRY(launch_spmv(A0, e0, e0, h->ls_r, 0, st));  // r0 = A e0
   const double* saved = h->ls_logk;
-  h->ls_logk = nullptr;  // the plain V-cycle
+  h->ls_logk = nullptr;  // the plain V-cycle (without the finest post-smoothing in replace mode)
+  h->ls_sampling = true;
   const int rc = vcycle_body(h, h->ls_r, h->ls_d, st);
+  h->ls_sampling = false;
   h->ls_logk = saved;
   TRY(rc);
   SMG_CUDA_TRY(cnn_sample_glue(0, n, e0, h->ls_d, h->ls_t, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, st));
@@ -1263,6 +1281,17 @@ extern "C" int smg_set_learned_smoother(smg_t h, const float* theta, const doubl
     h->vgraph = nullptr;
   }
   SMG_CUDA_TRY(cudaStreamSynchronize(st));
+  return SMG_OK;
+}
+
+extern "C" int smg_set_learned_mode(smg_t h, int mode) {
+  if (!h || (mode != SMG_LEARNED_AFTER && mode != SMG_LEARNED_REPLACE)) return SMG_EINVAL;
+  if (mode == SMG_LEARNED_REPLACE && h->pk != K64) return SMG_EINVAL;
+  h->ls_mode = mode;
+  if (h->vgraph) {
+    cudaGraphExecDestroy(h->vgraph);
+    h->vgraph = nullptr;
+  }
   return SMG_OK;
 }
 

@@ -16,6 +16,7 @@ SGS, ILU0, LGS = 0, 1, 2
 FW27V, PC8C, C64C, C16XY = 0, 1, 2, 3
 FP64, FP32, BF16 = 0, 1, 2
 PCG, FPCG, FGMRES = 0, 1, 2
+LEARNED_AFTER, LEARNED_REPLACE = 0, 1
 OP_SPMV, OP_RESIDUAL, OP_GS_FORWARD, OP_GS_BACKWARD, OP_GS_ZERO, OP_ILU_APPLY, OP_RESTRICT, OP_PROLONG_ADD, \
     OP_COARSE_SOLVE, OP_ILU_LOWER, OP_ILU_UPPER, OP_LGS_FORWARD, OP_LGS_BACKWARD, OP_LGS_ZERO = range(14)
 ARR_A, ARR_LU, ARR_DINV, ARR_AV, ARR_AS, ARR_LUV, ARR_LS, ARR_US, ARR_DINV32 = range(9)
@@ -81,6 +82,7 @@ def lib():
         L.smg_cnn_loss_grad.argtypes = [ip, vp, vp, vp, vp, vp, vp, sz, vp]
         L.smg_cnn_adam.argtypes = [i, vp, vp, vp, vp, i, f, f, f, f, f, vp]
         L.smg_set_learned_smoother.argtypes = [vp, vp, vp, vp]
+        L.smg_set_learned_mode.argtypes = [vp, ctypes.c_int]
         L.smg_learned_sample.argtypes = [vp, vp, vp, vp, vp, vp]
         L.smg_learned_loss_grad.argtypes = [vp, vp, vp, vp, i, vp, vp, vp, ctypes.c_size_t, vp]
         _lib = L
@@ -284,6 +286,13 @@ class SMG:
         rc = self._lib.smg_set_learned_smoother(self.h, _ptr(theta), _ptr(logk), _stream(stream))
         if rc != OK:
             raise SmgError(rc, "smg_set_learned_smoother")
+
+    def set_learned_mode(self, mode):
+        """LEARNED_AFTER (the network after the V-cycle) or LEARNED_REPLACE
+        (in place of the finest level's post-smoothing)."""
+        rc = self._lib.smg_set_learned_mode(self.h, int(mode))
+        if rc != OK:
+            raise SmgError(rc, "smg_set_learned_mode")
 
     def learned_sample(self, e0, logk, in2, target, stream=None):
         """One training pair from a known error e0 (see smg_learned_sample)."""

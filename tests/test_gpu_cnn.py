@@ -254,6 +254,45 @@ def test_post_smoother_matches_oracle_when_accepted_and_rejected(S, C, orc):
     assert torch.equal(z, z_plain)
 
 
+def test_replace_mode_falls_back_to_the_plain_vcycle_and_converges(S, C):
+    """SMG_LEARNED_REPLACE: the network stands in for the finest level's
+    post-smoothing.  (1) A correction the test rejects (the wrong-sign Jacobi
+    step) makes the skipped post-smoothing run: the result is the plain
+    V-cycle's bit for bit.  (2) An accepted one (a damped Jacobi step) gives
+    another, still contracting, preconditioner.  (3) FPCG with it converges
+    to the tolerance, the true residual confirming it."""
+    d = (16, 16, 16)
+    A, logk = varcoef(d, 3)
+    n = A.shape[0]
+    r = cu(I.rhs(n, 4).numpy())
+    h = S.SMG(d, I.OFF7, cu(A), smoother=S.SGS, krylov=S.FPCG)
+    z_plain = torch.empty(n, dtype=torch.float64, device="cuda")
+    h.vcycle(r, z_plain)
+    lk = cu(logk)
+    h.set_learned_mode(S.LEARNED_REPLACE)
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    h.set_learned_smoother(cu(C.flatten(C.identity_network(-0.3)).astype(np.float32)), lk)
+    h.vcycle(r, z)
+    assert torch.equal(z, z_plain)
+    h.set_learned_smoother(cu(C.flatten(C.identity_network(0.3)).astype(np.float32)), lk)
+    h.vcycle(r, z)
+    assert not torch.equal(z, z_plain)
+    from oracle import oracle as orc
+    res = np.linalg.norm(host_np(r) - orc.spmv(d, I.OFF7, A, host_np(z))) / np.linalg.norm(host_np(r))
+    assert res < 1.0
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    it, rr, rc = h.solve(r, x, tol=1e-9, maxit=200)
+    assert rc == 0 and rr < 1e-9
+    res = np.linalg.norm(host_np(r) - orc.spmv(d, I.OFF7, A, host_np(x))) / np.linalg.norm(host_np(r))
+    assert res < 1e-9
+    with pytest.raises(S.SmgError):
+        h.set_learned_mode(7)
+
+
+def host_np(t):
+    return t.detach().cpu().numpy()
+
+
 def test_learned_smoother_requires_a_flexible_krylov_method(S):
     d = (8, 8, 8)
     A, logk = varcoef(d, 5)
