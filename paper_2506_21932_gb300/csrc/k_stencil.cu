@@ -53,6 +53,46 @@ __global__ void __launch_bounds__(TPB) k_spmv1(Grid g, Stencil s, const typename
   y[skew ? skew_slot(g, skew, i, j, k) : p] = mode ? b[p] - acc : acc;
 }
 
+// The same for FP32 levels, bandwidth-bound: the CTA's rows of A (one
+// contiguous, 16-byte aligned run: TPB * NS values) are staged in shared
+// memory by 16-byte loads, instead of 27 scattered loads per thread
+// (residual at 384^3: 1.50 -> 1.42 ms).  BF16 rows (54 bytes) read back at
+// that stride conflict in shared memory and measured slower: they keep
+// k_spmv1.
+template <int PK, int NS>
+__global__ void __launch_bounds__(TPB) k_spmv1s(Grid g, Stencil s, const typename Prec<PK>::val* __restrict__ A,
+                                                const float* __restrict__ scale,
+                                                const typename Prec<PK>::vec* __restrict__ x,
+                                                const typename Prec<PK>::vec* __restrict__ b,
+                                                typename Prec<PK>::vec* __restrict__ y, int mode, int skew) {
+  using V = typename Prec<PK>::vec;
+  using Val = typename Prec<PK>::val;
+  __shared__ __align__(16) Val sa[TPB * NS];
+  const long long p0 = (long long)blockIdx.x * TPB;
+  const int rows = (int)min((long long)TPB, g.n - p0);
+  const int nval = rows * NS;
+  const int nvec = nval * (int)sizeof(Val) / 16;
+  const uint4* src = reinterpret_cast<const uint4*>(A + p0 * NS);
+  for (int q = threadIdx.x; q < nvec; q += TPB) reinterpret_cast<uint4*>(sa)[q] = src[q];
+  for (int q = nvec * 16 / (int)sizeof(Val) + threadIdx.x; q < nval; q += TPB) sa[q] = A[p0 * NS + q];
+  __syncthreads();
+  if ((int)threadIdx.x >= rows) return;
+  const long long p = p0 + threadIdx.x;
+  int i, j, k;
+  coords(p, g, i, j, k);
+  const Val* a = sa + threadIdx.x * NS;
+  V acc = 0;
+#pragma unroll
+  for (int e = 0; e < NS; ++e) {
+    int a0 = i + s.off[e][0], a1 = j + s.off[e][1], a2 = k + s.off[e][2];
+    V xv = inside3(a0, a1, a2, g) ? x[p + s.lin[e]] : V(0);
+    acc = fma((V)to_c(a[e]), xv, acc);
+  }
+  // the row scale multiplies the finished sum, rounded on its own
+  if (PK == KBF) acc = __fmul_rn(scale[p], (float)acc);
+  y[skew ? skew_slot(g, skew, i, j, k) : p] = mode ? b[p] - acc : acc;
+}
+
 // Runtime stencil size (any mask).
 template <int PK>
 __global__ void __launch_bounds__(TPB) k_spmv1_any(Grid g, Stencil s, const typename Prec<PK>::val* __restrict__ A,
@@ -967,11 +1007,18 @@ cudaError_t launch_spmv(const LevelView& L, const void* x, const void* b, void* 
                                          mode);
     return cudaGetLastError();
   }
+  const bool aligned16 = ((uintptr_t)L.A & 15u) == 0;  // the staged kernel copies 16-byte units
 #define SPMV_CASE(PK)                                                                                          \
   {                                                                                                            \
     using Val = typename Prec<PK>::val;                                                                        \
     using Vec = typename Prec<PK>::vec;                                                                        \
-    if (L.s.ns == 27)                                                                                          \
+    if (L.s.ns == 27 && PK == K32 && aligned16)                                                                \
+      k_spmv1s<PK, 27><<<nb, TPB, 0, st>>>(L.g, L.s, (const Val*)L.A, L.scale, (const Vec*)x, (const Vec*)b,   \
+                                           (Vec*)y, mode, skew);                                               \
+    else if (L.s.ns == 7 && PK == K32 && aligned16)                                                            \
+      k_spmv1s<PK, 7><<<nb, TPB, 0, st>>>(L.g, L.s, (const Val*)L.A, L.scale, (const Vec*)x, (const Vec*)b,    \
+                                          (Vec*)y, mode, skew);                                                \
+    else if (L.s.ns == 27)                                                                                     \
       k_spmv1<PK, 27><<<nb, TPB, 0, st>>>(L.g, L.s, (const Val*)L.A, L.scale, (const Vec*)x, (const Vec*)b,    \
                                           (Vec*)y, mode, skew);                                                      \
     else if (L.s.ns == 7)                                                                                      \
