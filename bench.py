@@ -39,6 +39,8 @@ WORKLOADS = {
     # the same problem at 128^3: the small case for detailed profiles (matrix 453 MB > L2)
     "c2_128": dict(desc="aniso27_128^3_ilu0_fw27v_pcg_fp64", dims=(128, 128, 128), gen="q1", smoother=1,
                    transfer=0, precision=0, krylov=0, tol=1e-9),
+    "c2_128_fp32": dict(desc="aniso27_128^3_ilu0_fw27v_fpcg_fp32hier", dims=(128, 128, 128), gen="q1", smoother=1,
+                        transfer=0, precision=1, krylov=1, tol=1e-9),
     # the largest configuration that fits one GPU (56.6 M unknowns), three ways:
     # FP64 hierarchy under PCG (value), FP32 and BF16 hierarchies under FPCG
     "c3": dict(desc="aniso27_384^3_ilu0_fw27v_pcg", dims=(384, 384, 384), gen="q1", smoother=1, transfer=0,
