@@ -208,6 +208,9 @@ int smg_level_info(smg_t h, int l, int dims[3], int* nstencil, int* offsets);
  * uint16 for BF16), 4 FP32 row scale of A [n], 5 low-precision ILU factors
  * ([n][ns] like 3: lower entries scaled by 6, upper by 7), 6 FP32 row scale of
  * L [n], 7 FP32 row scale of U [n], 8 FP32 inverse diagonal [n].
+ * On levels whose ILU(0) sweeps read the skewed records, 5-8 are not kept
+ * after set-up: the first request for one of them allocates and computes
+ * all four on `stream` (SMG_ENOMEM if that allocation fails).
  * Returns SMG_EINVAL if the array does not exist on that level or bytes is
  * smaller than its size; writes the size to *needed if not NULL. */
 int smg_level_copy(smg_t h, int l, int which, void* dst, size_t bytes, size_t* needed, void* stream);

@@ -545,6 +545,28 @@ static int plan_levels(const int d[3], int maxl, int transfer, int dims[][3]) {
   return L;
 }
 
+// ILU(0) factors and 1/u_pp in the V-cycle precision (FP32 / BF16 levels of
+// an ILU(0) hierarchy): lower entries scaled by Ls, upper ones by Us.
+// Idempotent; a no-op for FP64 and for the other smoothers.
+static int lower_factors(smg_ctx* h, Level& L, cudaStream_t st) {
+  if (h->pk == K64 || !L.LU || L.LUv) return SMG_OK;
+  const long long n = L.g.n;
+  const size_t vb = h->pk == K32 ? sizeof(float) : sizeof(__nv_bfloat16);
+  void *luv = nullptr, *dv = nullptr;
+  float *ls = nullptr, *us = nullptr;
+  TRY(dev_alloc(h, &luv, n * L.s.ns * vb));
+  TRY(dalloc(h, &ls, n));
+  TRY(dalloc(h, &us, n));
+  TRY(dev_alloc(h, &dv, n * sizeof(float)));
+  SMG_CUDA_TRY(launch_lower_matrix(L.g, L.s, L.LU, h->pk, 1, luv, ls, us, st));
+  SMG_CUDA_TRY(launch_d2f_array(L.udinv, (float*)dv, n, st));
+  L.LUv = luv;
+  L.Ls = ls;
+  L.Us = us;
+  L.dinv32 = dv;
+  return SMG_OK;
+}
+
 static int setup_level_smoother(smg_ctx* h, Level& L, cudaStream_t st) {
   const long long n = L.g.n;
   const int B = L.B;
@@ -591,15 +613,9 @@ static int setup_level_smoother(smg_ctx* h, Level& L, cudaStream_t st) {
       TRY(dev_alloc(h, &L.Av, n * L.s.ns * 9 * sizeof(float)));
       SMG_CUDA_TRY(launch_d2f_array(L.A, (float*)L.Av, n * L.s.ns * 9, st));
     }
-    TRY(dev_alloc(h, &L.dinv32, n * B * B * sizeof(float)));
     if (h->opt.smoother == SMG_SMOOTHER_SGS) {
+      TRY(dev_alloc(h, &L.dinv32, n * B * B * sizeof(float)));
       SMG_CUDA_TRY(launch_d2f_array(L.dinv, (float*)L.dinv32, n * B * B, st));
-    } else {
-      TRY(dev_alloc(h, &L.LUv, n * L.s.ns * vb));
-      TRY(dalloc(h, &L.Ls, n));
-      TRY(dalloc(h, &L.Us, n));
-      SMG_CUDA_TRY(launch_lower_matrix(L.g, L.s, L.LU, h->pk, 1, L.LUv, L.Ls, L.Us, st));
-      SMG_CUDA_TRY(launch_d2f_array(L.udinv, (float*)L.dinv32, n, st));
     }
   }
   // point smoothers on the warp-pipelined kernel read records of the skewed
@@ -620,6 +636,9 @@ static int setup_level_smoother(smg_ctx* h, Level& L, cudaStream_t st) {
     TRY(dev_alloc(h, &L.vs0, (size_t)n * vsize(h)));
     TRY(dev_alloc(h, &L.vs1, (size_t)n * vsize(h)));
   }
+  // the natural-order sweeps read the factors in the V-cycle precision; the
+  // skewed levels' records were built from the FP64 factors directly
+  if (!skewed(L)) TRY(lower_factors(h, L, st));
   return SMG_OK;
 }
 
@@ -1084,11 +1103,14 @@ extern "C" int smg_level_info(smg_t h, int l, int dims[3], int* nstencil, int* o
 
 extern "C" int smg_level_copy(smg_t h, int l, int which, void* dst, size_t bytes, size_t* needed, void* stream) {
   if (!h || l < 0 || l >= h->nlev) return SMG_EINVAL;
-  const Level& L = h->L[l];
+  Level& L = h->L[l];
   const long long n = L.g.n;
   const size_t vb = h->pk == K32 ? 4 : 2;
   const void* src = nullptr;
   size_t sz = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  // skewed levels keep no lowered factors; they are made on first request
+  if (which >= 5 && which <= 8) TRY(lower_factors(h, L, st));
   switch (which) {
     case 0: src = L.A; sz = n * L.s.ns * L.B * L.B * 8; break;
     case 1: src = L.LU; sz = n * L.s.ns * 8; break;
@@ -1105,7 +1127,6 @@ extern "C" int smg_level_copy(smg_t h, int l, int which, void* dst, size_t bytes
   if (needed) *needed = sz;
   if (!dst) return SMG_OK;
   if (bytes < sz) return SMG_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
   SMG_CUDA_TRY(cudaMemcpyAsync(dst, src, sz, cudaMemcpyDeviceToDevice, st));
   SMG_CUDA_TRY(cudaStreamSynchronize(st));
   return SMG_OK;
