@@ -1022,35 +1022,37 @@ static void residual32(const orc_level* L, int B, const float* b, const float* x
 }
 
 /* One point of Gauss-Seidel in FP32: g = b_p - sum_{o != 0} A_po u_{p+o}, then
- * u_p = dinv_p g (scalar) or u_p = Dinv_p g (3x3 block, row by row). */
-static void gs32_point(const orc_level* L, int B, const float* b, float* u, int i, int j, int k) {
+ * v = dinv_p g (scalar) or v = Dinv_p g (3x3 block, row by row), and with a
+ * weight w != 1 the Sec. 4.4 update u_p = (1-w) u_p + w v, all in float. */
+static void gs32_point(const orc_level* L, int B, const float* b, float* u, double w, int i, int j, int k) {
   const int* d = L->d;
   long p = pidx(d, i, j, k);
   float t[3], g[3];
   rowsum32(L, B, u, i, j, k, 1, t);
   for (int c = 0; c < B; ++c) g[c] = b[p * B + c] - t[c];
-  if (B == 1) {
-    u[p] = g[0] * L->Dv32[p];
-    return;
-  }
+  const float wf = (float)w;
   for (int r = 0; r < B; ++r) {
     float v = 0.0f;
-    for (int c = 0; c < B; ++c) v += L->Dv32[(p * B + r) * B + c] * g[c];
-    u[p * B + r] = v;
+    if (B == 1) {
+      v = g[0] * L->Dv32[p];
+    } else {
+      for (int c = 0; c < B; ++c) v += L->Dv32[(p * B + r) * B + c] * g[c];
+    }
+    u[p * B + r] = (w == 1.0) ? v : (1.0f - wf) * u[p * B + r] + wf * v;
   }
 }
 
-/* Gauss-Seidel sweep in FP32, dir +1 lexicographic, -1 reverse. */
-static void gs32(const orc_level* L, int B, const float* b, float* u, int dir) {
+/* Gauss-Seidel sweep in FP32 with weight w, dir +1 lexicographic, -1 reverse. */
+static void gs32(const orc_level* L, int B, const float* b, float* u, double w, int dir) {
   const int* d = L->d;
   if (dir > 0) {
     for (int i = 0; i < d[0]; ++i)
       for (int j = 0; j < d[1]; ++j)
-        for (int k = 0; k < d[2]; ++k) gs32_point(L, B, b, u, i, j, k);
+        for (int k = 0; k < d[2]; ++k) gs32_point(L, B, b, u, w, i, j, k);
   } else {
     for (int i = d[0] - 1; i >= 0; --i)
       for (int j = d[1] - 1; j >= 0; --j)
-        for (int k = d[2] - 1; k >= 0; --k) gs32_point(L, B, b, u, i, j, k);
+        for (int k = d[2] - 1; k >= 0; --k) gs32_point(L, B, b, u, w, i, j, k);
   }
 }
 
@@ -1146,8 +1148,8 @@ static void vcycle32(orc_mg* mg, const double* r, double* z) {
     float* res = (float*)malloc(sizeof(float) * n);
     if (mg->smoother == SM_SGS) {
       for (long t = 0; t < n; ++t) u[l][t] = 0.0f;
-      gs32(L, B, f[l], u[l], +1);
-      gs32(L, B, f[l], u[l], -1);
+      gs32(L, B, f[l], u[l], mg->w, +1);
+      gs32(L, B, f[l], u[l], mg->w, -1);
     } else {
       ilu32(L, f[l], u[l]);
     }
@@ -1168,8 +1170,8 @@ static void vcycle32(orc_mg* mg, const double* r, double* z) {
     long n = npts(L->d) * B;
     prolong32(mg->transfer, L->d, B, u[l + 1], u[l]);
     if (mg->smoother == SM_SGS) {
-      gs32(L, B, f[l], u[l], +1);
-      gs32(L, B, f[l], u[l], -1);
+      gs32(L, B, f[l], u[l], mg->w, +1);
+      gs32(L, B, f[l], u[l], mg->w, -1);
     } else {
       float *res = (float*)malloc(sizeof(float) * n), *x = (float*)malloc(sizeof(float) * n);
       residual32(L, B, f[l], u[l], res);
@@ -1197,7 +1199,7 @@ int orc_mg_level_apply32(void* h, int l, int op, float* x, const float* b, float
     case 0: if (!L->Av) return ORC_EINVAL; residual32(L, mg->B, b, x, y); return ORC_OK;
     case 1: case 2:
       if (mg->smoother != SM_SGS || !L->Av) return ORC_EINVAL;
-      gs32(L, mg->B, b, x, op == 1 ? +1 : -1);
+      gs32(L, mg->B, b, x, mg->w, op == 1 ? +1 : -1);
       return ORC_OK;
     case 3: if (mg->smoother != SM_ILU0 || !L->Lv) return ORC_EINVAL; ilu32(L, b, y); return ORC_OK;
     case 4: if (last) return ORC_EINVAL; restrict32(mg->transfer, L->d, mg->B, x, y); return ORC_OK;

@@ -143,6 +143,27 @@ def test_gauss_seidel_sweeps_exact_equal_fp64(orc, prec, B):
     assert exact_ints(g64) and np.array_equal(g32.astype(np.float64), g64)
 
 
+@pytest.mark.parametrize("prec,B", [(1, 1), (2, 1), (1, 3)])
+def test_weighted_gauss_seidel_sweeps_exact_equal_fp64(orc, prec, B):
+    """With w = 1/2 the Sec. 4.4 update (1 - w) u_p + w v only halves, so on
+    the cell-coupled integer data the weighted FP32 / BF16 sweeps equal the
+    weighted FP64 sweeps bit for bit; a dropped or misplaced weight breaks
+    the equality (the weight changes the result, checked below)."""
+    A = cell_matrix(D8, 5, B=B)
+    mg = orc.MG(D8, OFF27, A, B=B, smoother=orc.SGS, transfer=orc.PC8C, w=0.5, precision=prec, max_levels=2)
+    Dinv = orc.diag_inverse(D8, OFF27, A, B=B)
+    b, u0 = small_ints(N8 * B, 7, 20), small_ints(N8 * B, 8, 20)
+    f64 = orc.gs_forward(D8, OFF27, A, Dinv, b, u0, w=0.5, B=B)
+    assert not np.array_equal(f64, orc.gs_forward(D8, OFF27, A, Dinv, b, u0, B=B))
+    f32 = mg.level_apply32(0, 1, x=u0, b=b)
+    assert np.array_equal(f64.astype(np.float32).astype(np.float64), f64)  # every value exact in FP32
+    assert np.array_equal(f32.astype(np.float64), f64)
+    g64 = orc.gs_backward(D8, OFF27, A, Dinv, b, f64, w=0.5, B=B)
+    g32 = mg.level_apply32(0, 2, x=f32, b=b)
+    assert np.array_equal(g64.astype(np.float32).astype(np.float64), g64)
+    assert np.array_equal(g32.astype(np.float64), g64)
+
+
 @pytest.mark.parametrize("prec", [1, 2])
 def test_ilu_apply_exact_equals_fp64(orc, prec):
     """The FP32 / BF16 ILU(0) application (L solve with the lower row scale,
