@@ -267,7 +267,8 @@ def run_ours(args, w, rank, world):
         # a reduced-precision hierarchy is only approximately symmetric: PCG
         # becomes flexible PCG (FGMRES stays)
         kry = w["krylov"] if (prec == 0 or w["krylov"] == 2) else 1
-        return dict(block=B, smoother=w["smoother"], transfer=w["transfer"], precision=prec, krylov=kry, restart=30)
+        return dict(block=B, smoother=w["smoother"], transfer=w["transfer"], precision=prec, krylov=kry, restart=30,
+                    sweep_warps=args.sweep_warps)
 
     theta, learned_info = (None, None)
     if w.get("learned"):
@@ -568,6 +569,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
+    ap.add_argument("--sweep-warps", type=int, default=0, choices=[0, 1, 2],
+                    help="warps per strip of the wavefront sweeps (0: the library's choice)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", 0))

@@ -104,7 +104,15 @@ enum { SMG_KRYLOV_PCG = 0, SMG_KRYLOV_FPCG = 1, SMG_KRYLOV_FGMRES = 2 };
  *                    the same order either way.  Off by default: the fine
  *                    residual is FP64-bound, and the fused pass's tile-edge
  *                    recomputation and lower occupancy cost more than the
- *                    fine-residual traffic it saves (measured on GB300). */
+ *                    fine-residual traffic it saves (measured on GB300).
+ *  sweep_warps [0]   warps per 32-column strip of the point smoothers'
+ *                    wavefront sweeps on 19/27-point levels: 1 one warp
+ *                    does everything; 2 a helper warp loads the operands and
+ *                    forms the early partial sums while the main warp only
+ *                    finishes points (not for FP64 Gauss-Seidel with old
+ *                    values, nor for y extents above 256, which keep one);
+ *                    0 the library's choice.  Same arithmetic in the same
+ *                    order either way. */
 typedef struct {
   int smoother, transfer, precision, krylov, restart;
   double relax_w;
@@ -112,6 +120,7 @@ typedef struct {
   int spin_budget_ms;
   int use_graph;
   int fuse_restrict;
+  int sweep_warps;
 } smg_options;
 
 /* Build the hierarchy from the finest matrix (Sec. 4.2: only the finest A is
@@ -242,6 +251,15 @@ enum {
   SMG_OP_LGS_ZERO = 13
 };
 int smg_level_apply(smg_t h, int l, int op, const void* x, const void* b, void* y, void* stream);
+
+/* Warps per 32-column strip of the wavefront kernel that runs the point
+ * sweep `op` (SMG_OP_GS_FORWARD / GS_BACKWARD / GS_ZERO / ILU_LOWER /
+ * ILU_UPPER) of level l, in the V-cycle and in smg_level_apply: 2 the two-
+ * warp kernel (option sweep_warps), 1 the one-warp warp-pipelined kernel,
+ * 0 another kernel (or the level has no such sweep).  Host-only: reports the
+ * choice the launch makes, launches nothing.  Errors: -SMG_EINVAL for a bad
+ * handle, level or op. */
+int smg_level_sweep_warps(smg_t h, int l, int op);
 
 /* Number of CUDA kernels this library has enqueued since it was loaded (a
  * V-cycle replayed from a CUDA graph counts its kernels on every replay).

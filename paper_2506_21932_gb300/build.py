@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["smg_api.cu", "k_stencil.cu", "k_sweep.cu", "k_sweep2.cu", "k_sweep3.cu", "k_sweep3_f32.cu", "k_sweep3_bf16.cu", "k_ilu3.cu", "k_bsweep3.cu", "k_lsweep.cu", "k_setup.cu", "k_krylov.cu",
+SOURCES = ["smg_api.cu", "k_stencil.cu", "k_sweep.cu", "k_sweep2.cu", "k_sweep3.cu", "k_sweep3_f32.cu", "k_sweep3_bf16.cu", "k_sweep3h_f64.cu", "k_sweep3h_f32.cu", "k_sweep3h_bf16.cu", "k_ilu3.cu", "k_bsweep3.cu", "k_lsweep.cu", "k_setup.cu", "k_krylov.cu",
            "k_cnn.cu", "cnn_api.cu", "noalloc.cu", "chains.cpp"]
 
 

@@ -1,10 +1,14 @@
 // Dispatch of the warp-pipelined wavefront sweeps (kernel in sweep3.cuh) and
 // the FP64 instantiations.
 #include "sweep3.cuh"
+#include "sweep3h.cuh"
 
 using namespace sweep3;
 
 namespace {
+
+// Whether the library picks the two-warp sweeps where they apply.
+constexpr bool kHelperByDefault = true;
 
 int planes_per_cta(const LevelView& L) {
   const int NW = (L.g.ny + 31) / 32;
@@ -33,6 +37,18 @@ bool sweep3_supported(const LevelView& L, int kind) {
   return (size_t)((L.g.nx + W - 1) / W) * NW <= (size_t)kProgSlots;
 }
 
+// Planes per CTA of the two-warp kernel: two for FP32 / BF16 when both fit.
+static int helper_planes(const LevelView& L) {
+  const int NW = (L.g.ny + 31) / 32;
+  return (L.pk != K64 && NW <= kHelperMaxStrips / 2) ? 2 : 1;
+}
+
+int sweep3_warps(const LevelView& L, int kind, bool rec, const SweepCfg& cfg) {
+  if (!sweep3_supported(L, kind)) return 0;
+  const bool want = cfg.warps == 2 || (cfg.warps == 0 && kHelperByDefault);
+  return (rec && want && helper_applies(L.pk, L.s.ns, L.g.nx, L.g.ny, helper_planes(L), kind)) ? 2 : 1;
+}
+
 // Planes per CTA: FP64 sweeps are bound by the FP64 pipe, so one plane per
 // CTA keeps the per-SM work at one plane; FP32 / BF16 sweeps are bound by
 // synchronisation latency, so two planes share a CTA and every other plane
@@ -57,7 +73,18 @@ cudaError_t launch_sweep3(const LevelView& L, int kind, int dir, const void* M, 
   P.ws = ws;
   P.err = err;
   for (int e = 0; e < 27; ++e) P.lin[e] = L.s.lin[e];
-  cudaError_t e;
+  cudaError_t e = cudaErrorNotSupported;
+  // two warps per strip (sweep3h.cuh) where they apply and are asked for
+  if (sweep3_warps(L, kind, rec, cfg) == 2) {
+    const int Wh = helper_planes(L);
+    if (L.pk == K64) e = sweep3h_launch_k64(ns, kind, dir, P, st);
+    else if (L.pk == K32) e = sweep3h_launch_k32(ns, Wh, kind, dir, P, st);
+    else e = sweep3h_launch_kbf(ns, Wh, kind, dir, P, st);
+    if (e != cudaErrorNotSupported) {
+      smg_count_launch(1);
+      return e;
+    }
+  }
   if (L.pk == K64) e = sweep3_launch_k64(ns, kind, dir, rec, P, st);
   else if (L.pk == K32) e = sweep3_launch_k32(ns, W, kind, dir, rec, P, st);
   else e = sweep3_launch_kbf(ns, W, kind, dir, rec, P, st);

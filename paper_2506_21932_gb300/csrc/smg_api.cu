@@ -579,6 +579,7 @@ static int setup_level_smoother(smg_ctx* h, Level& L, cudaStream_t st) {
   // (at the price of a G-step larger lag between consecutive planes)
   L.cfg.G = 4;
   L.cfg.budget_ns = (unsigned long long)h->opt.spin_budget_ms * 1000000ull;
+  L.cfg.warps = h->opt.sweep_warps;
   TRY(dalloc(h, &L.ws, 1));
   SMG_CUDA_TRY(cudaMemsetAsync(L.ws, 0, sizeof(SweepWs), st));
   if (h->opt.smoother == SMG_SMOOTHER_LGS) {
@@ -845,6 +846,7 @@ extern "C" int smg_setup(smg_t* out, const int dims[3], int nstencil, const int*
   if (o.max_levels < 0) return SMG_EINVAL;
   if (o.spin_budget_ms <= 0) o.spin_budget_ms = 1000;
   if (o.fuse_restrict < 0 || o.fuse_restrict > 1) return SMG_EINVAL;
+  if (o.sweep_warps < 0 || o.sweep_warps > 2) return SMG_EINVAL;
   if (block == 3 && (o.smoother != SMG_SMOOTHER_SGS || o.precision == SMG_PREC_BF16)) return SMG_EINVAL;
   if (o.smoother == SMG_SMOOTHER_ILU0 && nstencil != 7 && nstencil != 19 && nstencil != 27) return SMG_EINVAL;
   // line Gauss-Seidel: scalar FP64 hierarchy, weight 1, columns of at most 1024 points
@@ -1085,6 +1087,25 @@ extern "C" int smg_solve(smg_t h, const double* b, double* x, double tol, int ma
 // level-wise building blocks
 // ---------------------------------------------------------------------------
 extern "C" int smg_level_count(smg_t h) { return h ? h->nlev : 0; }
+
+extern "C" int smg_level_sweep_warps(smg_t h, int l, int op) {
+  if (!h || l < 0 || l >= h->nlev) return -SMG_EINVAL;
+  int kind;
+  switch (op) {
+    case SMG_OP_GS_FORWARD:
+    case SMG_OP_GS_BACKWARD: kind = SW_GS_FULL; break;
+    case SMG_OP_GS_ZERO: kind = SW_GS_ZERO; break;
+    case SMG_OP_ILU_LOWER: kind = SW_ILU_L; break;
+    case SMG_OP_ILU_UPPER: kind = SW_ILU_U; break;
+    default: return -SMG_EINVAL;
+  }
+  Level& L = h->L[l];
+  const bool ilu_op = kind == SW_ILU_L || kind == SW_ILU_U;
+  if (ilu_op != (h->opt.smoother == SMG_SMOOTHER_ILU0) || h->opt.smoother == SMG_SMOOTHER_LGS) return 0;
+  // the warp-pipelined kernels run a level's point sweeps exactly when its
+  // records are in the skewed layout
+  return skewed(L) ? sweep3_warps(view(h, L, true), kind, true, L.cfg) : 0;
+}
 
 extern "C" int smg_level_info(smg_t h, int l, int dims[3], int* nstencil, int* offsets) {
   if (!h || l < 0 || l >= h->nlev) return SMG_EINVAL;

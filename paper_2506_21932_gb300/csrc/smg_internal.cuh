@@ -172,6 +172,7 @@ struct SweepCfg {
   int SA, SB;  // schedule skews: global time t = SA*i + SB*j + k
   int G;       // publish progress every G steps
   unsigned long long budget_ns;
+  int warps = 0;  // warps per 32-column strip of the skewed-layout sweeps: 0 the library's choice, 1, 2
 };
 cudaError_t launch_sweep(const LevelView& L, int kind, int dir, const void* M, const float* sc1, const float* sc2,
                          const void* dinv, double w, const void* b, void* u, SweepWs* ws, int* err,
@@ -191,6 +192,9 @@ cudaError_t launch_sweep2(const LevelView& L, int kind, int dir, const void* M, 
 // ilurec.cuh (FP32 / BF16 sweeps exist only in that form); otherwise M is
 // the matrix or ILU factors [n][ns] and the vectors are in natural order.
 bool sweep3_supported(const LevelView& L, int kind);
+// Warps per 32-column strip launch_sweep3 uses for this sweep: 2 (the
+// two-warp kernel), 1 (the one-warp kernel), 0 (not supported).
+int sweep3_warps(const LevelView& L, int kind, bool rec, const SweepCfg& cfg);
 cudaError_t launch_sweep3(const LevelView& L, int kind, int dir, const void* M, const float* sc1, const float* sc2,
                           const void* dinv, double w, const void* b, void* u, SweepWs* ws, int* err,
                           const SweepCfg& cfg, cudaStream_t st, bool rec);

@@ -135,6 +135,11 @@ __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefe
 
 // 32-bit word wi of a record held in registers (wi a compile-time constant
 // after unrolling, so this is a register selection), and value `slot`.
+// Products that must not be contracted into a following add: the point
+// update rounds them on their own, the same in every sweep kernel.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <int CH>
 __device__ __forceinline__ unsigned rec_word(const uint4 (&q)[CH], int wi) {
   const uint4 v = q[wi >> 2];
@@ -167,6 +172,74 @@ struct Shared3 {
   int abort;
   int group;
 };
+
+// Publisher warp: lane w publishes the progress of warp w of the CTA's last
+// plane (wd: that plane's counters, local steps) as global time gt0 + T with
+// a GPU-scope release store whenever it grows.
+template <class SH>
+__device__ __forceinline__ void publisher_warp(SH& sh, const int* wd, const Sweep3Params& P, int I, int NW, int gt0,
+                                               int lane) {
+  const bool mine = lane < NW;
+  int* out_slot = P.ws->prog + (size_t)I * NW + lane;
+  int published = INT_MIN;
+  for (;;) {
+    const int T = mine ? ld_acq_cta(&wd[lane]) : kDone;
+    if (__any_sync(0xffffffffu, mine && T != published)) {
+      // one release (one GPU-scope fence) covers every lane's value; a
+      // fence also stalls the SM's other memory traffic, so they are
+      // spaced by a fraction of a step
+      if (mine) st_release(out_slot, T >= kDone ? kDone : gt0 + T);
+      published = T;
+      if (__all_sync(0xffffffffu, T >= kDone)) break;
+      __nanosleep(kPublishGapNs);
+    } else {
+      __nanosleep(32);
+    }
+    if (__any_sync(0xffffffffu, ld_acq_cta(&sh.abort) != 0)) {
+      // release everything downstream; the error word is already set
+      if (mine) st_release(out_slot, kDone);
+      break;
+    }
+  }
+}
+
+// Poller warp: lane w forwards the progress of warp w of the previous CTA's
+// last plane into sh.avail (GPU-scope acquire loads).  Bounded: the previous
+// CTA must make progress within the budget, else the error word and the
+// CTA's abort flag are set.
+template <class SH>
+__device__ __forceinline__ void poller_warp(SH& sh, const Sweep3Params& P, int I, int NW, int lane) {
+  const bool mine = lane < NW;
+  const int* in_slot = P.ws->prog + (size_t)(I - 1) * NW + lane;
+  int seen = (I == 0 || !mine) ? kDone : 0;
+  unsigned long long t_wait = 0;
+  unsigned iter = 0;
+  while (__any_sync(0xffffffffu, seen < kDone)) {
+    int v = seen;
+    if (seen < kDone) asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(in_slot) : "memory");
+    const bool fresh = v > seen;
+    bool stop = false;
+    if (__any_sync(0xffffffffu, fresh)) {
+      if (fresh) {
+        seen = v;
+        st_rel_cta(&sh.avail[lane], v);
+      }
+      t_wait = 0;
+    } else if (lane == 0) {
+      const unsigned long long now = globaltimer_ns();
+      if (t_wait == 0) t_wait = now;
+      else if (now - t_wait > P.budget_ns) {
+        atomicCAS(P.err, 0, DEV_ERR_TIMEOUT);
+        stop = true;
+      }
+    }
+    if ((++iter & 63u) == 0 && lane == 0) stop = stop || ld_relaxed(P.err) != 0 || ld_acq_cta(&sh.abort) != 0;
+    if (__shfl_sync(0xffffffffu, stop, 0)) {
+      if (lane == 0) st_rel_cta(&sh.abort, 1);
+      break;
+    }
+  }
+}
 
 // FP64 sweeps hold their operands in register pairs: they get at most 12
 // compute warps (ny <= 384) and the registers that leaves, 8 (ny <= 256)
@@ -225,66 +298,9 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
     __syncthreads();
 
     if (warp == ncompute) {
-      // ---- publisher warp: lane w publishes the progress of warp w of the
-      // CTA's last plane with a GPU-scope release store whenever it grows
-      const int plast = nplanes - 1;
-      const int gt0 = SA * (I * W + plast);
-      const bool mine = lane < NW;
-      int* out_slot = P.ws->prog + (size_t)I * NW + lane;
-      int published = INT_MIN;
-      for (;;) {
-        const int T = mine ? ld_acq_cta(&sh.wdone[plast][lane]) : kDone;
-        if (__any_sync(0xffffffffu, mine && T != published)) {
-          // one release (one GPU-scope fence) covers every lane's value; a
-          // fence also stalls the SM's other memory traffic, so they are
-          // spaced by a fraction of a step
-          if (mine) st_release(out_slot, T >= kDone ? kDone : gt0 + T);
-          published = T;
-          if (__all_sync(0xffffffffu, T >= kDone)) break;
-          __nanosleep(kPublishGapNs);
-        } else {
-          __nanosleep(32);
-        }
-        if (__any_sync(0xffffffffu, ld_acq_cta(&sh.abort) != 0)) {
-          // release everything downstream; the error word is already set
-          if (mine) st_release(out_slot, kDone);
-          break;
-        }
-      }
+      publisher_warp(sh, sh.wdone[nplanes - 1], P, I, NW, SA * (I * W + nplanes - 1), lane);
     } else if (warp == ncompute + 1) {
-      // ---- poller warp: lane w forwards the progress of warp w of the
-      // previous CTA's last plane into shared memory (GPU-scope acquire loads)
-      const bool mine = lane < NW;
-      const int* in_slot = P.ws->prog + (size_t)(I - 1) * NW + lane;
-      int seen = (I == 0 || !mine) ? kDone : 0;
-      unsigned long long t_wait = 0;
-      unsigned iter = 0;
-      while (__any_sync(0xffffffffu, seen < kDone)) {
-        int v = seen;
-        if (seen < kDone) asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(in_slot) : "memory");
-        const bool fresh = v > seen;
-        bool stop = false;
-        if (__any_sync(0xffffffffu, fresh)) {
-          if (fresh) {
-            seen = v;
-            st_rel_cta(&sh.avail[lane], v);
-          }
-          t_wait = 0;
-        } else if (lane == 0) {
-          // bounded: the previous CTA must make progress within the budget
-          const unsigned long long now = globaltimer_ns();
-          if (t_wait == 0) t_wait = now;
-          else if (now - t_wait > P.budget_ns) {
-            atomicCAS(P.err, 0, DEV_ERR_TIMEOUT);
-            stop = true;
-          }
-        }
-        if ((++iter & 63u) == 0 && lane == 0) stop = stop || ld_relaxed(P.err) != 0 || ld_acq_cta(&sh.abort) != 0;
-        if (__shfl_sync(0xffffffffu, stop, 0)) {
-          if (lane == 0) st_rel_cta(&sh.abort, 1);
-          break;
-        }
-      }
+      poller_warp(sh, P, I, NW, lane);
     } else if (warp < W * NW) {
       // ---- compute warp (p, w)
       const int p = warp / NW, w = warp % NW;
@@ -558,13 +574,13 @@ __global__ void __launch_bounds__(max_threads<PK, KIND>(), 1) k_sweep3(Sweep3Par
               }
               a = fma(sg * (V)to_c(cfK[e]), tv, a);
             }
-            if (PK == KBF) a = (V)sK * a;
+            if (PK == KBF) a = mul_rn((V)sK, a);
             V r;
             if (KIND == SW_ILU_L) {
               r = FOLD ? a : bK - a;
             } else {
               r = (FOLD ? a : bK - a) * dK;
-              if (KIND != SW_ILU_U && relax) r = (KIND == SW_GS_ZERO) ? wv * r : (V(1) - wv) * uoK + wv * r;
+              if (KIND != SW_ILU_U && relax) r = (KIND == SW_GS_ZERO) ? wv * r : fma(wv, r, mul_rn(V(1) - wv, uoK));
             }
             u[SPLIT ? vbase + (long long)rs * g.ny : vslot(0, 0, kK)] = r;
             hp[(K & (kRing - 1)) * (NW * 32) + J] = r;

@@ -35,7 +35,7 @@ class Options(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("transfer", ctypes.c_int), ("precision", ctypes.c_int),
                 ("krylov", ctypes.c_int), ("restart", ctypes.c_int), ("relax_w", ctypes.c_double),
                 ("max_levels", ctypes.c_int), ("spin_budget_ms", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("fuse_restrict", ctypes.c_int)]
+                ("fuse_restrict", ctypes.c_int), ("sweep_warps", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -65,6 +65,7 @@ def lib():
         L.smg_strerror.restype = ctypes.c_char_p
         L.smg_level_count.argtypes = [vp]
         L.smg_level_info.argtypes = [vp, i, ip, ip, ip]
+        L.smg_level_sweep_warps.argtypes = [vp, i, i]
         L.smg_level_copy.argtypes = [vp, i, i, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), vp]
         L.smg_level_apply.argtypes = [vp, i, i, vp, vp, vp, vp]
         L.smg_derive_chains.argtypes = [i, i, ip, i, ip, i, ip, i, ip]
@@ -198,7 +199,7 @@ class SMG:
 
     def __init__(self, dims, offsets, coeffs, block=1, smoother=SGS, transfer=FW27V, precision=FP64,
                  krylov=PCG, restart=30, relax_w=1.0, max_levels=0, spin_budget_ms=0, use_graph=0, fuse_restrict=0,
-                 stream=None):
+                 sweep_warps=0, stream=None):
         import torch
         if not (coeffs.is_cuda and coeffs.dtype == torch.float64 and coeffs.is_contiguous()):
             raise ValueError("coeffs must be a contiguous float64 CUDA tensor")
@@ -208,7 +209,7 @@ class SMG:
         self.n = self.dims[0] * self.dims[1] * self.dims[2]
         self.precision = precision
         opt = Options(smoother, transfer, precision, krylov, restart, relax_w, max_levels, spin_budget_ms, use_graph,
-                      fuse_restrict)
+                      fuse_restrict, sweep_warps)
         offs = [c for o in offsets for c in o]
         h = ctypes.c_void_p()
         rc = self._lib.smg_setup(ctypes.byref(h), _iarr(self.dims), len(offsets), _iarr(offs),
@@ -260,6 +261,13 @@ class SMG:
         if rc != OK:
             raise SmgError(rc, "smg_level_info")
         return tuple(d), [tuple(off[3 * e:3 * e + 3]) for e in range(ns.value)]
+
+    def level_sweep_warps(self, l, op):
+        """Warps per strip of the kernel running sweep `op` on level l (0: another kernel)."""
+        rc = self._lib.smg_level_sweep_warps(self.h, l, op)
+        if rc < 0:
+            raise SmgError(-rc, "smg_level_sweep_warps")
+        return rc
 
     def level_array(self, l, which, stream=None):
         """Copies a level array into a new uint8 CUDA tensor and returns it."""

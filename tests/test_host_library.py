@@ -129,6 +129,8 @@ def test_setup_rejects_bad_arguments(smg):
     assert _setup_status(smg, (4, 4, 4), I.OFF7, opt=bad) == (smg.EINVAL, None)
     bad = smg.Options(0, 0, 0, 2, 99, 1.0, 0, 0, 0)  # restart > 64
     assert _setup_status(smg, (4, 4, 4), I.OFF7, opt=bad) == (smg.EINVAL, None)
+    bad = smg.Options(0, 0, 0, 0, 0, 1.0, 0, 0, 0, 0, 3)  # warps per sweep strip outside 0..2
+    assert _setup_status(smg, (4, 4, 4), I.OFF7, opt=bad) == (smg.EINVAL, None)
     L = smg.lib()
     assert L.smg_setup(None, None, 0, None, None, 1, None, None) == smg.EINVAL
     assert L.smg_vcycle(None, None, None, None) == smg.EINVAL
