@@ -101,11 +101,11 @@ FP64_PROBE = os.path.join(ROOT, "profiles", "fp64_fma_peak_gb300.txt")
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per point of the
 # dominant kernel, from one ncu capture of the current kernel on the same
 # problem family at a smaller size (the traffic grows with the points); keyed
-# by (smoother, stencil points, precision).  Absent where no capture of the
-# current kernel exists.
+# by (kernel, smoother, stencil points, precision).  Absent where no capture
+# of the current kernel exists.
 TRAFFIC_PER_POINT = {
     # k_sweep3 ILU lower solve, FP64, 27 points: 268.97 MB for 128^3
-    (1, 27, 0): (268.970e6 / 128 ** 3, "profiles/k_sweep3_ilu_lower_aniso27_128cubed.md"),
+    ("k_sweep3", 1, 27, 0): (268.970e6 / 128 ** 3, "profiles/k_sweep3_ilu_lower_aniso27_128cubed.md"),
 }
 
 
@@ -364,6 +364,7 @@ def run_ours(args, w, rank, world):
     z = torch.empty_like(b)
     vcycles = {}
     main_profile = None
+    lvl0_warps = 0
     for prec in forms:
         h = smg.SMG(w["dims"], off, A, **opts(prec))
         s = h.stats()
@@ -379,6 +380,9 @@ def run_ours(args, w, rank, world):
         torch.cuda.synchronize()
         vc_ms = e0.elapsed_time(e1) / nv
         profs = [h.vcycle_profile(b, z) for _ in range(3)]
+        if prec == main_prec and w["smoother"] != 2:
+            # which wavefront kernel runs the level-0 sweep the roofline reports
+            lvl0_warps = h.level_sweep_warps(0, smg.OP_ILU_LOWER if w["smoother"] == 1 else smg.OP_GS_ZERO)
         h.close()
         stage = {}
         for prof in profs:
@@ -417,17 +421,18 @@ def run_ours(args, w, rank, world):
         fac_pt = 8.0 * ((m - 1) * 5 + 17) * 128 / nz
         flops_pt, bytes_pt = 2 * (nlow - 1) + 10, nlow * cbytes + fac_pt + 2 * vbytes
     elif w["smoother"] == 1:
-        kname = "k_sweep3 (ILU(0) lower solve, level 0)"
+        kfile = "k_sweep3h" if lvl0_warps == 2 else "k_sweep3"
+        kname = "%s (ILU(0) lower solve, level 0)" % kfile
         flops_pt, bytes_pt = 2 * nlow + 1, nlow * cbytes + 2 * vbytes + sbytes
     else:
-        kfile = ("k_sweep3" if ny <= 512 else "k_sweep2") if B == 1 else "k_bsweep3"
+        kfile = {2: "k_sweep3h", 1: "k_sweep3"}.get(lvl0_warps, "k_sweep2") if B == 1 else "k_bsweep3"
         kname = "%s (Gauss-Seidel zero-guess forward, level 0)" % kfile
         flops_pt = (2 * nlow + 2) * B * B
         bytes_pt = nlow * cbytes * B * B + vbytes * B * B + 2 * vbytes * B + sbytes
     k_ms = main_profile[(0, "pre1")]
     hbm = float(measured_peaks().get("hbm_gbs", HBM_PEAK_FALLBACK))
     k_gbs = lvl0 * bytes_pt / (k_ms * 1e-3) / 1e9
-    tr = TRAFFIC_PER_POINT.get((w["smoother"], nsf, main_prec)) if B == 1 else None
+    tr = TRAFFIC_PER_POINT.get((kfile, w["smoother"], nsf, main_prec)) if B == 1 and w["smoother"] != 2 else None
     traffic = None if tr is None else round(tr[0] * lvl0)
     hbm_roof = {"achieved": round(k_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(k_gbs / hbm, 4),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in measured_peaks()
