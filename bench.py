@@ -106,6 +106,8 @@ FP64_PROBE = os.path.join(ROOT, "profiles", "fp64_fma_peak_gb300.txt")
 TRAFFIC_PER_POINT = {
     # k_sweep3 ILU lower solve, FP64, 27 points: 268.97 MB for 128^3
     ("k_sweep3", 1, 27, 0): (268.970e6 / 128 ** 3, "profiles/k_sweep3_ilu_lower_aniso27_128cubed.md"),
+    # k_sweep3h (two warps per strip), same solve: 268.25 MB for 128^3
+    ("k_sweep3h", 1, 27, 0): (268.252e6 / 128 ** 3, "profiles/k_sweep3h_ilu_lower_aniso27_128cubed.md"),
 }
 
 
