@@ -37,10 +37,10 @@ bool sweep3_supported(const LevelView& L, int kind) {
   return (size_t)((L.g.nx + W - 1) / W) * NW <= (size_t)kProgSlots;
 }
 
-// Planes per CTA of the two-warp kernel: two for FP32 / BF16 when both fit.
+// Planes per CTA of the two-warp kernel: two when both fit.
 static int helper_planes(const LevelView& L) {
   const int NW = (L.g.ny + 31) / 32;
-  return (L.pk != K64 && NW <= kHelperMaxStrips / 2) ? 2 : 1;
+  return NW <= kHelperMaxStrips / 2 ? 2 : 1;
 }
 
 int sweep3_warps(const LevelView& L, int kind, bool rec, const SweepCfg& cfg) {
@@ -77,7 +77,7 @@ cudaError_t launch_sweep3(const LevelView& L, int kind, int dir, const void* M, 
   // two warps per strip (sweep3h.cuh) where they apply and are asked for
   if (sweep3_warps(L, kind, rec, cfg) == 2) {
     const int Wh = helper_planes(L);
-    if (L.pk == K64) e = sweep3h_launch_k64(ns, kind, dir, P, st);
+    if (L.pk == K64) e = sweep3h_launch_k64(ns, Wh, kind, dir, P, st);
     else if (L.pk == K32) e = sweep3h_launch_k32(ns, Wh, kind, dir, P, st);
     else e = sweep3h_launch_kbf(ns, Wh, kind, dir, P, st);
     if (e != cudaErrorNotSupported) {

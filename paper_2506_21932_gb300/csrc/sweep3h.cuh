@@ -453,6 +453,6 @@ cudaError_t launch_kind_h(int kind, int dir, const Sweep3Params& P, cudaStream_t
 }  // namespace sweep3
 
 // One entry per working precision, each compiled in its own translation unit.
-cudaError_t sweep3h_launch_k64(int ns, int kind, int dir, const sweep3::Sweep3Params& P, cudaStream_t st);
+cudaError_t sweep3h_launch_k64(int ns, int W, int kind, int dir, const sweep3::Sweep3Params& P, cudaStream_t st);
 cudaError_t sweep3h_launch_k32(int ns, int W, int kind, int dir, const sweep3::Sweep3Params& P, cudaStream_t st);
 cudaError_t sweep3h_launch_kbf(int ns, int W, int kind, int dir, const sweep3::Sweep3Params& P, cudaStream_t st);
