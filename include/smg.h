@@ -109,9 +109,10 @@ enum { SMG_KRYLOV_PCG = 0, SMG_KRYLOV_FPCG = 1, SMG_KRYLOV_FGMRES = 2 };
  *                    wavefront sweeps on 19/27-point levels: 1 one warp
  *                    does everything; 2 a helper warp loads the operands and
  *                    forms the early partial sums while the main warp only
- *                    finishes points (not for FP64 Gauss-Seidel with old
- *                    values, nor for y extents above 256, which keep one);
- *                    0 the library's choice.  Same arithmetic in the same
+ *                    finishes points (FP64 Gauss-Seidel with old values,
+ *                    y extents above 384, and y extents above 256 except
+ *                    for FP64 ILU(0), keep one); 0 the library's choice
+ *                    (two where they apply).  Same arithmetic in the same
  *                    order either way. */
 typedef struct {
   int smoother, transfer, precision, krylov, restart;

@@ -31,9 +31,14 @@ struct Shared3h {
   int group;
 };
 
-// 8 strips x 2 warps + the two communication warps
+// 8 strips x 2 warps + the two communication warps.  FP64 ILU(0) solves on
+// planes of 9 to 12 strips (one per CTA) get an 832-thread instantiation
+// (72 registers a thread); FP32 / BF16 sweeps there measured no faster than
+// the one-warp kernel (BF16 2% slower at 384^3), which keeps them.
 constexpr int kHelperThreads = 576;
 constexpr int kHelperMaxStrips = 8;
+constexpr int kHelperWideThreads = 832;
+constexpr int kHelperWideStrips = 12;
 
 // finish terms of point K (the ones the main warp adds)
 template <int NS, int KIND, int DIR, int X>
@@ -65,8 +70,8 @@ __host__ __device__ constexpr size_t helper_smem_bytes(int NW, int W) {
                       (size_t)2 * nfields<NS, KIND, DIR, X>() * 32 * NW * W);
 }
 
-template <int PK, int NS, int KIND, int DIR, int W, int X>
-__global__ void __launch_bounds__(kHelperThreads, 1) k_sweep3h(Sweep3Params P) {
+template <int PK, int NS, int KIND, int DIR, int W, int X, int MT>
+__global__ void __launch_bounds__(MT, 1) k_sweep3h(Sweep3Params P) {
   using V = typename Prec<PK>::vec;
   using Val = typename Prec<PK>::val;
   using S = Shape<NS>;
@@ -405,12 +410,15 @@ __global__ void __launch_bounds__(kHelperThreads, 1) k_sweep3h(Sweep3Params P) {
 
 // Whether the two-warp kernel takes a sweep: 19 / 27-point masks (the 7-point
 // mask has no early terms to hand over), at most kHelperMaxStrips strips per
-// CTA, and not the FP64 Gauss-Seidel sweep with old values.  The caller
-// checks that records and vectors are in the skewed layout.
+// CTA except for the FP64 Gauss-Seidel sweep with old values (it would
+// spill), or, for the FP64 ILU(0) solves, one plane of at most
+// kHelperWideStrips strips.  The caller checks that records and vectors are
+// in the skewed layout.
 inline bool helper_applies(int pk, int ns, int nx, int ny, int W, int kind) {
   const int NW = (ny + 31) / 32;
-  return (ns == 19 || ns == 27) && W * NW <= kHelperMaxStrips && !(pk == K64 && kind == SW_GS_FULL) &&
-         (size_t)((nx + W - 1) / W) * NW <= (size_t)kProgSlots;
+  const bool fits = (W * NW <= kHelperMaxStrips && !(pk == K64 && kind == SW_GS_FULL)) ||
+                    (pk == K64 && W == 1 && NW <= kHelperWideStrips && (kind == SW_ILU_L || kind == SW_ILU_U));
+  return (ns == 19 || ns == 27) && fits && (size_t)((nx + W - 1) / W) * NW <= (size_t)kProgSlots;
 }
 
 template <int PK, int NS, int W, int X>
@@ -419,6 +427,7 @@ cudaError_t launch_kind_h(int kind, int dir, const Sweep3Params& P, cudaStream_t
   const int NW = (P.g.ny + 31) / 32;
   if (!helper_applies(PK, NS, P.g.nx, P.g.ny, W, kind)) return cudaErrorNotSupported;
   const int nthr = (2 * W * NW + 2) * 32;
+  const bool wide = W * NW > kHelperMaxStrips;  // the 832-thread instantiation
   int dev = 0, nsm = 0;
   cudaError_t ae = cudaGetDevice(&dev);
   if (ae == cudaSuccess) ae = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -432,8 +441,19 @@ cudaError_t launch_kind_h(int kind, int dir, const Sweep3Params& P, cudaStream_t
     kern<<<grid, nthr, smem, st>>>(P);
     return cudaGetLastError();
   };
+  if (wide) {
+    if constexpr (W == 1 && PK == K64) {
+      constexpr int T = kHelperWideThreads;
+      if (kind == SW_ILU_L)
+        return go(k_sweep3h<PK, NS, SW_ILU_L, 1, 1, X, T>, helper_smem_bytes<V, NS, SW_ILU_L, 1, X>(NW, 1));
+      if (kind == SW_ILU_U)
+        return go(k_sweep3h<PK, NS, SW_ILU_U, -1, 1, X, T>, helper_smem_bytes<V, NS, SW_ILU_U, -1, X>(NW, 1));
+    }
+    return cudaErrorNotSupported;
+  }
+  constexpr int T = kHelperThreads;
   if (kind == SW_GS_ZERO)
-    return go(k_sweep3h<PK, NS, SW_GS_ZERO, 1, W, X>, helper_smem_bytes<V, NS, SW_GS_ZERO, 1, X>(NW, W));
+    return go(k_sweep3h<PK, NS, SW_GS_ZERO, 1, W, X, T>, helper_smem_bytes<V, NS, SW_GS_ZERO, 1, X>(NW, W));
   if (kind == SW_GS_FULL) {
     // FP64 with every old-value term in flight needs more registers than
     // 576 threads leave (it would spill): the one-warp kernel runs it
@@ -441,13 +461,13 @@ cudaError_t launch_kind_h(int kind, int dir, const Sweep3Params& P, cudaStream_t
       return cudaErrorNotSupported;
     } else {
       if (dir > 0)
-        return go(k_sweep3h<PK, NS, SW_GS_FULL, 1, W, X>, helper_smem_bytes<V, NS, SW_GS_FULL, 1, X>(NW, W));
-      return go(k_sweep3h<PK, NS, SW_GS_FULL, -1, W, X>, helper_smem_bytes<V, NS, SW_GS_FULL, -1, X>(NW, W));
+        return go(k_sweep3h<PK, NS, SW_GS_FULL, 1, W, X, T>, helper_smem_bytes<V, NS, SW_GS_FULL, 1, X>(NW, W));
+      return go(k_sweep3h<PK, NS, SW_GS_FULL, -1, W, X, T>, helper_smem_bytes<V, NS, SW_GS_FULL, -1, X>(NW, W));
     }
   }
   if (kind == SW_ILU_L)
-    return go(k_sweep3h<PK, NS, SW_ILU_L, 1, W, X>, helper_smem_bytes<V, NS, SW_ILU_L, 1, X>(NW, W));
-  return go(k_sweep3h<PK, NS, SW_ILU_U, -1, W, X>, helper_smem_bytes<V, NS, SW_ILU_U, -1, X>(NW, W));
+    return go(k_sweep3h<PK, NS, SW_ILU_L, 1, W, X, T>, helper_smem_bytes<V, NS, SW_ILU_L, 1, X>(NW, W));
+  return go(k_sweep3h<PK, NS, SW_ILU_U, -1, W, X, T>, helper_smem_bytes<V, NS, SW_ILU_U, -1, X>(NW, W));
 }
 
 }  // namespace sweep3
