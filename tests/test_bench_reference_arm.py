@@ -37,3 +37,30 @@ def test_every_workload_has_a_label():
         assert w["smoother"] in (0, 1, 2) and w["transfer"] in (0, 1, 2, 3) and w["krylov"] in (0, 1, 2), name
         assert w["gen"] in ("lap", "q1", "q1z", "fv", "blk"), name
         assert len(w["dims"]) == 3 and w["tol"] > 0, name
+
+
+def test_traffic_constants_trace_to_the_committed_profiles():
+    """Every DRAM-bytes-per-point constant bench.py reports as
+    roofline.traffic is the dram read + write of the ncu summary it cites,
+    divided by the points of that capture (128^3), and stays within 1.2x of
+    the kernel's algorithmic bytes (a larger figure would mean re-reads)."""
+    import importlib.util
+    import re
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert bench.TRAFFIC_PER_POINT
+    for (kernel, smoother, ns, prec), (per_point, src) in bench.TRAFFIC_PER_POINT.items():
+        path = os.path.join(ROOT, src)
+        assert os.path.exists(path), src
+        text = open(path).read()
+        assert kernel in text.splitlines()[0], (kernel, src)
+        m = re.search(r"\| dram read / write \| ([0-9.]+) MB / ([0-9.]+) MB", text)
+        assert m, src
+        captured = (float(m.group(1)) + float(m.group(2))) * 1e6 / 128 ** 3
+        assert abs(captured - per_point) <= 2e-3 * per_point, (src, captured, per_point)
+        # ILU(0) lower solve: n_low coefficients + b + u per point
+        assert smoother == 1 and ns == 27
+        c = {0: 8, 1: 4, 2: 2}[prec]
+        algorithmic = 13 * c + 2 * (8 if prec == 0 else 4) + (4 if prec == 2 else 0)
+        assert algorithmic <= per_point <= 1.2 * algorithmic, (src, per_point, algorithmic)
